@@ -1,0 +1,340 @@
+"""Benchmark of the SPH timestep on the rotating square patch.
+
+Default workload: 200^3 = 8,000,000 particles, FP32-mixed path, one step =
+neighbour search + density/EOS + momentum/energy + Courant dt + update +
+conserved sums.  Metric: pair interactions per second = sum_i |N(i)| x 2
+pair phases (density, momentum) per step / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+replica of the patch (the path does not shard; replicas only) and the slowest
+rank's time is used.  --impl reference times the FP64 CPU oracle, the
+correctness authority, on host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH pair-interactions/s & steps/s, 8M-particle patch, FP32-mixed vs FP64"
+UNIT = "pair-interactions/s"
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# FP32 operations per pair (FMA = 2, MUFU not counted), counted by hand from
+# k_momentum_mixed and k_density_mixed (see the per-line count in the design doc)
+FLOPS_PER_PAIR_MOMENTUM = 80
+FLOPS_PER_PAIR_DENSITY = 28
+
+WORKLOADS = {
+    "c1": ("square patch 20^3 (8,000 particles), omega=5", 20),
+    "c2": ("square patch 100^3 (1,000,000 particles), omega=5", 100),
+    "c3": ("square patch 200^3 (8,000,000 particles), omega=5", 200),
+}
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sample_n=100, nsteps=1):
+    """The FP64 oracle (as it stands) on host cores, one full step on the
+    100^3 patch: the same rotating-patch workload at 1/8 of the particles."""
+    import oracle
+    from paper_1905_03344_gb300 import inputs
+    f = inputs.square_patch(sample_n)
+    threads = os.cpu_count() or 1
+    sim = oracle.Sim(f, nthreads=threads)
+    t0 = time.perf_counter()
+    pairs = 0
+    for _ in range(nsteps):
+        sim.step(1)
+        pairs += sim.nnz
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d full oracle step(s) (neighbours..update) on the %d^3 square patch "
+                      "(%d particles), OpenMP on all host cores; %.1f s" % (nsteps, sample_n,
+                                                                            sample_n ** 3, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1905_03344_gb300 import inputs
+    n_edge = 100
+    f = inputs.square_patch(n_edge)
+    threads = os.cpu_count() or 1
+    sim = oracle.Sim(f, nthreads=threads)
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    pairs = 0
+    for _ in range(args.steps):
+        sim.step(1)
+        pairs += sim.nnz
+    el = time.perf_counter() - t0
+    val = 2.0 * pairs / el
+    wl = WORKLOADS[args.config][0]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl, "precision": "fp64 (CPU oracle)",
+                   "sample": "%d^3 square patch per step" % n_edge},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "each step: one full FP64 oracle step on the %d^3 square patch "
+                                   "(%d particles), the %s workload at 1/8 of its particles"
+                                   % (n_edge, n_edge ** 3, args.config)},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay the step as a CUDA graph")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1905_03344_gb300 import binding, build, inputs
+    build.build()
+    wl, n_edge = WORKLOADS[args.config]
+    f = inputs.square_patch(n_edge)
+    n = len(f["x"])
+    stream = torch.cuda.current_stream()
+    dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
+
+    def make(precision, graph=False):
+        sim = binding.SPH(n, precision=precision, stream=stream.cuda_stream,
+                          use_graph=int(graph), max_pairs=int(160 * n))
+        sim.set_particles(dfields)
+        return sim
+
+    sim = make(args.precision, args.graph)
+    if not args.no_autotune:
+        sim.autotune()
+        sim.set_particles(dfields)
+    tpp, cf = binding.sph_get_tuning(sim.ctx)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    sim.pair_count(reset=True)
+    if not args.graph:
+        sim.profile(True)
+        sim.profile()      # reset accumulators
+    clocks = Clocks(local)
+    l0 = sim.launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = sim.launches() - l0
+    pairs = sim.pair_count(reset=True)
+    prof = sim.profile() if not args.graph else {}
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+        p = torch.tensor([pairs], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(p, op=torch.distributed.ReduceOp.SUM)
+        pairs_all = float(p.item())
+    else:
+        pairs_all = float(pairs)
+    sec = ms_total / 1e3
+    value = 2.0 * pairs_all / sec
+    steps_per_s = args.steps / sec
+    pairs_per_step = pairs / args.steps
+
+    # dominant kernel: momentum/energy pair sum (FP32 pipe)
+    peaks, peak_src = measured_peaks()
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * (peaks.get("sm_max_mhz") or SM_MAX_MHZ) * 1e6 / 1e12
+    roof = None
+    if prof:
+        mom_ms = prof["momentum"][0] / max(args.steps, 1)
+        achieved = FLOPS_PER_PAIR_MOMENTUM * pairs_per_step / (mom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_momentum_mixed" if args.precision == "mixed" else "k_momentum_fp64",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None,
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
+                               % (SMS, FP32_LANES_PER_SM, peaks.get("sm_max_mhz") or SM_MAX_MHZ),
+                "flops_per_pair": FLOPS_PER_PAIR_MOMENTUM, "ms_per_launch": mom_ms}
+        if clk.get("sm_mhz"):
+            roof["frac_at_sampled_clock"] = achieved / (fp32_peak * clk["sm_mhz"] / (peaks.get("sm_max_mhz") or SM_MAX_MHZ))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-mixed (f32 pair sums + Kahan, f64 positions/integration/reductions)"
+        if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl, "particles": n, "precision": args.precision,
+                   "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
+                         % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
+                   "threads_per_particle": tpp, "cell_factor": cf, "graph": bool(args.graph)},
+        "steps_per_s": steps_per_s, "pairs_per_step": pairs_per_step,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if prof:
+        line["phase_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
+    if roof:
+        line["roofline"] = roof
+
+    # FP64 GPU path on the same patch
+    if args.fp64_steps > 0 and args.precision == "mixed":
+        sim.close()
+        s64 = make("fp64")
+        s64.step(1)
+        torch.cuda.synchronize()
+        s64.pair_count(reset=True)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.fp64_steps):
+            s64.step(1)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1) / args.fp64_steps
+        p64 = s64.pair_count(reset=True) / args.fp64_steps
+        line["fp64_path"] = {"value": 2.0 * p64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                             "steps_per_s": 1e3 / ms64, "steps": args.fp64_steps}
+        line["mixed_over_fp64"] = line["ms_per_step"] and ms64 / line["ms_per_step"]
+        s64.close()
+        sim = make(args.precision)
+        sim.autotune() if not args.no_autotune else None
+
+    # end to end through the C ABI with host (pinned) buffers
+    if args.e2e_steps > 0:
+        hfields = {k: torch.tensor(v, dtype=torch.float64).pin_memory() for k, v in f.items()}
+        sim.pair_count(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_particles(hfields)
+            sim.step(1)
+            sim.conserved()
+        el = time.perf_counter() - t0
+        pe = sim.pair_count(reset=True)
+        line["e2e"] = {"value": 2.0 * pe / el, "unit": UNIT, "h2d_bytes_per_step": 9 * 8 * n,
+                       "d2h_bytes_per_step": 7 * 8 + 8, "steps": args.e2e_steps,
+                       "ms_per_step": 1e3 * el / args.e2e_steps,
+                       "call": "sph_set_particles(host) + sph_step(1) + sph_conserved per step"}
+    sim.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * sph.h -- C ABI of the GB300 SPH timestep library (libsph_gb300.so).
+ *
+ * One timestep of the SPH-EXA mini-app's vanilla SPH solver on the rotating
+ * square patch (arXiv 1905.03344): neighbour discovery (Table 1), density
+ * summation and equation of state, momentum and energy equations with
+ * artificial viscosity, Courant time-step, Press (leapfrog) positions and
+ * Adams-Bashforth energy (Sec. 3), for one or many independent patches.
+ * The paper describes the mini-app's parts as independent libraries with
+ * interfaces generic enough to be called from any production code (Sec. 1);
+ * this header is that interface: plain C types, no C++ or torch types.
+ *
+ * Conventions (apply to every entry point):
+ *  - Every call returns sph_status; no exception, exit() or device trap ever
+ *    crosses this boundary.  sph_last_error(ctx) gives a one-line message.
+ *  - A CUDA error that poisons the context (a sticky error) puts the context
+ *    in SPH_ESTATE; afterwards only sph_destroy is valid.
+ *  - Particle fields are exchanged in the caller's particle order ("original
+ *    order").  Internally particles are kept sorted by (patch, Morton cell)
+ *    and the library keeps the permutation.
+ *  - on_device = 1: pointers are device pointers readable/writable on the
+ *    context's stream (e.g. torch tensors' data_ptr()).  on_device = 0: host
+ *    pointers; the call copies synchronously.
+ *  - All work is issued on the stream given in sph_config.cuda_stream (or a
+ *    library-owned stream when NULL).  Calls that return host-visible values
+ *    synchronise that stream.
+ *  - Inputs are copied: the caller keeps ownership of every pointer it
+ *    passes.  Pointers the library returns are borrowed and stay valid until
+ *    the next call that changes the particles or the neighbour lists.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_EINVAL = 1,      /* bad argument or configuration */
+    SPH_ENOMEM = 2,      /* device or host allocation failed */
+    SPH_ECUDA = 3,       /* a CUDA call failed (non-sticky) */
+    SPH_EOVERFLOW = 4,   /* neighbour list exceeded max_pairs; state left at the
+                            start of the failing step, particles re-sorted */
+    SPH_ENONFINITE = 5,  /* NaN/Inf in density, pressure, dt or inputs */
+    SPH_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+    SPH_ESTATE = 7       /* call out of order, or context poisoned */
+} sph_status;
+
+enum { SPH_FP64 = 0, SPH_MIXED = 1 };               /* sph_config.precision */
+enum { SPH_KERNEL_WENDLAND = 0 };                   /* sph_config.kernel */
+
+/* Fields for sph_get_field (all returned as double, original order). */
+enum {
+    SPH_FIELD_X = 0, SPH_FIELD_Y, SPH_FIELD_Z,
+    SPH_FIELD_VX, SPH_FIELD_VY, SPH_FIELD_VZ,     /* v_{n+1/2} after a step */
+    SPH_FIELD_M, SPH_FIELD_H, SPH_FIELD_U,
+    SPH_FIELD_DU_PREV,                            /* du of the last step */
+    SPH_FIELD_AXP, SPH_FIELD_AYP, SPH_FIELD_AZP,  /* a of the last step */
+    SPH_FIELD_RHO, SPH_FIELD_P, SPH_FIELD_C,      /* from the last density call */
+    SPH_FIELD_AX, SPH_FIELD_AY, SPH_FIELD_AZ, SPH_FIELD_DU, /* last momentum call */
+    SPH_FIELD_NOWN,                               /* n_i = #{j : r^2 < 4 h_i^2} */
+    SPH_FIELD_NNB,                                /* |N(i)| (symmetric union) */
+    SPH_FIELD_COUNT
+};
+
+typedef struct {
+    int32_t precision;      /* SPH_FP64 or SPH_MIXED (FP32 pair sums, Kahan) */
+    int32_t kernel;         /* SPH_KERNEL_WENDLAND (Eq. 2) */
+    double gamma;           /* ideal-gas exponent, 5/3 */
+    double n_target;        /* target neighbour count of h adaptation, 100 */
+    double courant;         /* Courant factor C, 0.2 */
+    double dt_growth;       /* dt_n <= dt_growth * dt_{n-1}, 1.1 */
+    double av_alpha, av_beta, av_eps;  /* Monaghan viscosity, 1, 2, 0.01 */
+    double lz;              /* period along z, 1 */
+    double dt_fixed;        /* > 0: fixed dt instead of the Courant condition */
+    int32_t adapt_h;        /* 1: h adaptation after each step */
+    int32_t threads_per_particle; /* 0 = auto; else 1, 2, 4, 8, 16 or 32 */
+    double cell_factor;     /* cell edge = 2 h_max * cell_factor, in [0.5, 4] */
+    int64_t max_particles;  /* capacity, <= 2^25 */
+    int64_t max_pairs;      /* neighbour-list capacity; 0 = 160 * max_particles */
+    int32_t max_patches;    /* capacity of independent patches, <= 256 */
+    int32_t use_graph;      /* 1: sph_step replays a captured CUDA graph */
+    void* cuda_stream;      /* cudaStream_t or NULL */
+} sph_config;
+
+/* Fills the defaults listed above (max_particles = 1<<20, max_patches = 1). */
+void sph_config_default(sph_config* cfg);
+
+/* Creates a context and allocates all device memory for the capacities in
+ * cfg.  Errors: SPH_EINVAL (bad cfg), SPH_ENOMEM, SPH_ECUDA (no device). */
+sph_status sph_create(const sph_config* cfg, sph_ctx** out);
+
+/* Frees everything; ctx may be NULL. */
+void sph_destroy(sph_ctx* ctx);
+
+/* Message of the last failing call on ctx (ctx may be NULL: global message). */
+const char* sph_last_error(const sph_ctx* ctx);
+const char* sph_status_string(sph_status s);
+
+/* Sets n particles (0 <= n <= max_particles); arrays of n doubles each, in the
+ * caller's order: position, velocity (v_{-1/2} := v_0), mass, smoothing
+ * length, specific internal energy.  Resets the time state (step 0,
+ * dt_{-1} = 0, du_{-1} = 0, a_{-1} = 0) and makes all particles one patch.
+ * Errors: SPH_EINVAL (n out of range, NULL pointer), SPH_ECUDA. */
+sph_status sph_set_particles(sph_ctx* ctx, int64_t n, const double* x, const double* y,
+                             const double* z, const double* vx, const double* vy,
+                             const double* vz, const double* m, const double* h,
+                             const double* u, int on_device);
+
+/* Splits the particles into independent patches: patch p is particles
+ * [offsets[p], offsets[p+1]) of the original order, offsets[0] = 0,
+ * offsets[n_patches] = n.  Each patch has its own grid, time-step and
+ * conserved sums, and its own z period lz.  Valid only right after
+ * sph_set_particles (or sph_set_state).  offsets is a host array.
+ * Errors: SPH_EINVAL, SPH_ESTATE. */
+sph_status sph_set_patches(sph_ctx* ctx, int32_t n_patches, const int64_t* offsets);
+
+/* Neighbour discovery (Table 1): per patch bounding box and Morton keys,
+ * radix sort into cells, cell ranges, neighbour counts, exclusive scan and
+ * CSR fill.  j is a neighbour of i iff j != i and r_ij^2 < 4 h_i^2 or
+ * r_ij^2 < 4 h_j^2 (minimum image along z), decided exactly in FP64.
+ * Errors: SPH_EOVERFLOW (more than max_pairs entries), SPH_ESTATE. */
+sph_status sph_find_neighbors(sph_ctx* ctx);
+
+/* Borrowed device pointers to the last neighbour lists, in sorted order:
+ * row k (sorted particle k) holds col[off[k] .. off[k+1]) as sorted indices;
+ * perm[k] is the original index of sorted particle k.  Within a row, columns
+ * are grouped by stencil cell.  Any output pointer may be NULL. */
+sph_status sph_get_neighbors(sph_ctx* ctx, const uint64_t** off, const uint32_t** col,
+                             const uint32_t** perm, int64_t* nnz);
+
+/* Copies the last neighbour lists into caller buffers (device or host per
+ * on_device): off (n+1 uint64), col (nnz uint32, sorted indices), perm (n
+ * uint32).  Any pointer may be NULL.  Same layout as sph_get_neighbors. */
+sph_status sph_copy_neighbors(sph_ctx* ctx, uint64_t* off, uint32_t* col, uint32_t* perm,
+                              int on_device);
+
+/* Density summation rho_i = m_i W(0,h_i) + sum_j m_j W(r_ij, h_i) (Sec. 3,
+ * Eq. 2) and the ideal-gas EOS P = (gamma-1) rho u, c = sqrt(gamma P/rho), on
+ * the current neighbour lists.  Errors: SPH_ESTATE (no lists),
+ * SPH_ENONFINITE. */
+sph_status sph_density(sph_ctx* ctx);
+
+/* Momentum and energy pair sums with Monaghan viscosity (Sec. 3):
+ *   a_i  = -sum_j m_j (P_i/rho_i^2 + P_j/rho_j^2 + Pi_ij) grad_i Wbar_ij
+ *   du_i =  sum_j m_j (P_i/rho_i^2 + Pi_ij/2) v_ij . grad_i Wbar_ij
+ * with Wbar_ij = (W(r,h_i) + W(r,h_j))/2 and the time-centred velocity
+ * v_{n-1/2} + a_{n-1} dt_{n-1}/2.  Errors: SPH_ESTATE (no density). */
+sph_status sph_momentum_energy(sph_ctx* ctx);
+
+/* nsteps full timesteps: neighbours, density + EOS, momentum + energy,
+ * Courant dt_n = min(C min h/c, dt_growth dt_{n-1}) per patch, kick
+ * v_{n+1/2} = v_{n-1/2} + a_n (dt_n + dt_{n-1})/2, drift x += v_{n+1/2} dt_n
+ * (z wrapped), Adams-Bashforth energy, h adaptation, conserved sums.
+ * dt_last (nullable, host) receives patch 0's last dt.
+ * Errors: SPH_EOVERFLOW, SPH_ENONFINITE, SPH_ETIMEOUT, SPH_ESTATE. */
+sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last);
+
+/* Conserved sums of patch (or all patches for patch = -1) from the current
+ * state, out (host) = { M, Px, Py, Pz, Lz, Ekin, Eint }: M = sum m,
+ * P = sum m v, Lz = sum m (x v_y - y v_x), Ekin = sum m v^2/2, Eint = sum m u,
+ * computed in FP64 with a deterministic two-level reduction. */
+sph_status sph_conserved(sph_ctx* ctx, int32_t patch, double out[7]);
+
+/* Copies one field (SPH_FIELD_*) in original order into dst (n doubles). */
+sph_status sph_get_field(sph_ctx* ctx, int32_t field, double* dst, int on_device);
+
+/* Time state of a patch: last dt, the dt used as dt_{n-1}, steps taken. */
+sph_status sph_get_dt(sph_ctx* ctx, int32_t patch, double* dt, double* dt_prev, int64_t* step);
+
+/* Checkpoint: with buf = NULL, *bytes receives the size needed; otherwise the
+ * full time state (particle fields in internal order, permutation, patch
+ * table, dt state) is written to the host buffer buf.  sph_set_state restores
+ * it; stepping then continues bit for bit as without the checkpoint. */
+sph_status sph_get_state(sph_ctx* ctx, void* buf, size_t* bytes);
+sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes);
+
+/* Times the neighbour and pair-sum phases for a few candidate launch
+ * configurations (threads per particle, cell factor) on the current
+ * particles and keeps the fastest; the particle state is left unchanged. */
+sph_status sph_autotune(sph_ctx* ctx);
+
+/* Current launch configuration (after sph_autotune or as configured). */
+sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* cell_factor);
+
+/* Phase timers: when enabled, every phase of sph_step/sph_find_neighbors/
+ * sph_density/sph_momentum_energy is bracketed by CUDA events on the
+ * context's stream (graph replay is then off).  sph_get_profile returns the
+ * accumulated milliseconds and launch counts per phase (SPH_PHASE_*) and
+ * resets them. */
+enum {
+    SPH_PHASE_BBOX = 0, SPH_PHASE_KEYS, SPH_PHASE_SORT, SPH_PHASE_GATHER, SPH_PHASE_NB_COUNT,
+    SPH_PHASE_NB_SCAN, SPH_PHASE_NB_FILL, SPH_PHASE_DENSITY, SPH_PHASE_MOMENTUM,
+    SPH_PHASE_UPDATE, SPH_PHASE_COUNT
+};
+sph_status sph_set_profiling(sph_ctx* ctx, int enable);
+sph_status sph_get_profile(sph_ctx* ctx, double* ms, int64_t* launches, int32_t nphase);
+
+/* Number of kernels this context has launched so far (graph replays count
+ * every kernel node). */
+sph_status sph_get_launch_count(sph_ctx* ctx, int64_t* launches);
+
+/* Neighbour-list size of the last sph_find_neighbors. */
+sph_status sph_get_nnz(sph_ctx* ctx, int64_t* nnz);
+
+/* Sum of |N(i)| over all particles and all sph_step steps since the last
+ * reset (the pair-interaction count of the steps); reset != 0 zeroes it. */
+sph_status sph_get_pair_count(sph_ctx* ctx, int64_t* total, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_GB300_H */

@@ -1,0 +1,389 @@
+"""Python binding of the C ABI in include/sph.h (libsph_gb300.so).
+
+Argument marshalling only: every step of the SPH timestep runs in the CUDA
+kernels behind the C ABI.  Functions carry the names of the C entry points;
+`SPH` is a small object wrapper over one context.  Device arrays are torch
+CUDA tensors (float64 / int64 / int32, contiguous); host arrays are numpy.
+
+The library must be built first (`python -m paper_1905_03344_gb300.build` or
+`__graft_entry__.build()`); there is no CPU fallback: a missing library or a
+missing GPU raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EOVERFLOW, SPH_ENONFINITE, SPH_ETIMEOUT, SPH_ESTATE = range(8)
+SPH_FP64, SPH_MIXED = 0, 1
+SPH_KERNEL_WENDLAND = 0
+
+FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "h", "u", "du_prev", "axp", "ayp", "azp",
+          "rho", "P", "c", "ax", "ay", "az", "du", "nown", "nnb"]
+FIELD = {k: i for i, k in enumerate(FIELDS)}
+PHASES = ["bbox", "keys", "sort", "gather", "nb_count", "nb_scan", "nb_fill", "density",
+          "momentum", "update"]
+
+
+class SphConfig(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("n_target", ctypes.c_double),
+                ("courant", ctypes.c_double), ("dt_growth", ctypes.c_double),
+                ("av_alpha", ctypes.c_double), ("av_beta", ctypes.c_double),
+                ("av_eps", ctypes.c_double), ("lz", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("adapt_h", ctypes.c_int32),
+                ("threads_per_particle", ctypes.c_int32), ("cell_factor", ctypes.c_double),
+                ("max_particles", ctypes.c_int64), ("max_pairs", ctypes.c_int64),
+                ("max_patches", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class SphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+STATUS_NAMES = {0: "SPH_OK", 1: "SPH_EINVAL", 2: "SPH_ENOMEM", 3: "SPH_ECUDA",
+                4: "SPH_EOVERFLOW", 5: "SPH_ENONFINITE", 6: "SPH_ETIMEOUT", 7: "SPH_ESTATE"}
+
+# exported symbols and their (restype, argtypes); the test suite checks this
+# list against include/sph.h
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_ST = ctypes.c_int
+SIGNATURES = {
+    "sph_config_default": (None, [ctypes.POINTER(SphConfig)]),
+    "sph_create": (_ST, [ctypes.POINTER(SphConfig), ctypes.POINTER(_P)]),
+    "sph_destroy": (None, [_P]),
+    "sph_last_error": (ctypes.c_char_p, [_P]),
+    "sph_status_string": (ctypes.c_char_p, [_ST]),
+    "sph_set_particles": (_ST, [_P, _I64] + [_P] * 9 + [ctypes.c_int]),
+    "sph_set_patches": (_ST, [_P, _I32, _P]),
+    "sph_find_neighbors": (_ST, [_P]),
+    "sph_get_neighbors": (_ST, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                               ctypes.POINTER(_I64)]),
+    "sph_copy_neighbors": (_ST, [_P, _P, _P, _P, ctypes.c_int]),
+    "sph_density": (_ST, [_P]),
+    "sph_momentum_energy": (_ST, [_P]),
+    "sph_step": (_ST, [_P, _I32, ctypes.POINTER(_D)]),
+    "sph_conserved": (_ST, [_P, _I32, _P]),
+    "sph_get_field": (_ST, [_P, _I32, _P, ctypes.c_int]),
+    "sph_get_dt": (_ST, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "sph_get_state": (_ST, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "sph_set_state": (_ST, [_P, _P, ctypes.c_size_t]),
+    "sph_autotune": (_ST, [_P]),
+    "sph_get_tuning": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
+    "sph_set_profiling": (_ST, [_P, ctypes.c_int]),
+    "sph_get_profile": (_ST, [_P, _P, _P, _I32]),
+    "sph_get_launch_count": (_ST, [_P, ctypes.POINTER(_I64)]),
+    "sph_get_nnz": (_ST, [_P, ctypes.POINTER(_I64)]),
+    "sph_get_pair_count": (_ST, [_P, ctypes.POINTER(_I64), ctypes.c_int]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads libsph_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libsph_gb300.so is not built (%s); run __graft_entry__.build() or "
+                              "python -m paper_1905_03344_gb300.build" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st):
+    if st != SPH_OK:
+        msg = lib().sph_last_error(ctx)
+        raise SphError(st, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, on_device) of a torch tensor or numpy array (contiguous)."""
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+def sph_config_default():
+    c = SphConfig()
+    lib().sph_config_default(ctypes.byref(c))
+    return c
+
+
+def sph_create(cfg=None):
+    if cfg is None:
+        cfg = sph_config_default()
+    h = ctypes.c_void_p()
+    st = lib().sph_create(ctypes.byref(cfg), ctypes.byref(h))
+    if st != SPH_OK:
+        raise SphError(st, lib().sph_last_error(None).decode())
+    return h
+
+
+def sph_destroy(ctx):
+    lib().sph_destroy(ctx)
+
+
+def sph_set_particles(ctx, fields):
+    """fields: dict with x y z vx vy vz m h u, each float64 of length n (all
+    torch CUDA tensors, or all numpy arrays)."""
+    names = ["x", "y", "z", "vx", "vy", "vz", "m", "h", "u"]
+    arrs = [fields[k] for k in names]
+    n = len(arrs[0])
+    ptrs = []
+    dev = None
+    for a in arrs:
+        if not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+        p, d = _ptr(a)
+        dev = d if dev is None else dev
+        if d != dev or len(a) != n:
+            raise ValueError("fields must all be device tensors or all host arrays, of equal length")
+        ptrs.append((p, a))
+    _check(ctx, lib().sph_set_particles(ctx, n, *[p for p, _ in ptrs], dev))
+
+
+def sph_set_patches(ctx, offsets):
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(ctx, lib().sph_set_patches(ctx, len(o) - 1, ctypes.c_void_p(o.ctypes.data)))
+
+
+def sph_find_neighbors(ctx):
+    _check(ctx, lib().sph_find_neighbors(ctx))
+
+
+def sph_get_nnz(ctx):
+    v = ctypes.c_int64()
+    _check(ctx, lib().sph_get_nnz(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def sph_get_neighbors(ctx):
+    """Borrowed device pointers (off, col, perm, nnz) as integers."""
+    o, c, p = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    nnz = ctypes.c_int64()
+    _check(ctx, lib().sph_get_neighbors(ctx, ctypes.byref(o), ctypes.byref(c), ctypes.byref(p),
+                                        ctypes.byref(nnz)))
+    return o.value, c.value, p.value, nnz.value
+
+
+def sph_copy_neighbors(ctx, n, device=None):
+    """(off int64[n+1], col int32[nnz], perm int32[n]) as torch tensors on
+    `device`, or numpy arrays when device is None."""
+    nnz = sph_get_nnz(ctx)
+    if device is None:
+        off = np.zeros(n + 1, dtype=np.uint64)
+        col = np.zeros(max(nnz, 1), dtype=np.uint32)
+        perm = np.zeros(max(n, 1), dtype=np.uint32)
+        _check(ctx, lib().sph_copy_neighbors(ctx, ctypes.c_void_p(off.ctypes.data),
+                                             ctypes.c_void_p(col.ctypes.data),
+                                             ctypes.c_void_p(perm.ctypes.data), 0))
+        return off.astype(np.int64), col[:nnz].astype(np.int64), perm[:n].astype(np.int64)
+    import torch
+    off = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    col = torch.zeros(max(nnz, 1), dtype=torch.int32, device=device)
+    perm = torch.zeros(max(n, 1), dtype=torch.int32, device=device)
+    _check(ctx, lib().sph_copy_neighbors(ctx, ctypes.c_void_p(off.data_ptr()),
+                                         ctypes.c_void_p(col.data_ptr()),
+                                         ctypes.c_void_p(perm.data_ptr()), 1))
+    return off, col[:nnz], perm[:n]
+
+
+def sph_density(ctx):
+    _check(ctx, lib().sph_density(ctx))
+
+
+def sph_momentum_energy(ctx):
+    _check(ctx, lib().sph_momentum_energy(ctx))
+
+
+def sph_step(ctx, nsteps=1):
+    dt = ctypes.c_double()
+    _check(ctx, lib().sph_step(ctx, int(nsteps), ctypes.byref(dt)))
+    return dt.value
+
+
+def sph_conserved(ctx, patch=-1):
+    out = np.zeros(7)
+    _check(ctx, lib().sph_conserved(ctx, int(patch), ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def sph_get_field(ctx, field, n, out=None):
+    """Field (name or SPH_FIELD_* index) in original order.  With out (a
+    float64 torch CUDA tensor or numpy array of length n) fills it; otherwise
+    returns a new numpy array."""
+    f = FIELD[field] if isinstance(field, str) else int(field)
+    if out is not None:
+        p, d = _ptr(out)
+        _check(ctx, lib().sph_get_field(ctx, f, p, d))
+        return out
+    res = np.zeros(max(n, 1))
+    p, d = _ptr(res)
+    _check(ctx, lib().sph_get_field(ctx, f, p, d))
+    return res[:n]
+
+
+def sph_get_dt(ctx, patch=0):
+    dt, dtp, step = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, lib().sph_get_dt(ctx, int(patch), ctypes.byref(dt), ctypes.byref(dtp),
+                                 ctypes.byref(step)))
+    return dt.value, dtp.value, step.value
+
+
+def sph_get_state(ctx):
+    nb = ctypes.c_size_t()
+    _check(ctx, lib().sph_get_state(ctx, None, ctypes.byref(nb)))
+    buf = ctypes.create_string_buffer(nb.value)
+    _check(ctx, lib().sph_get_state(ctx, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(nb)))
+    return buf.raw[: nb.value]
+
+
+def sph_set_state(ctx, blob):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(ctx, lib().sph_set_state(ctx, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+
+
+def sph_autotune(ctx):
+    _check(ctx, lib().sph_autotune(ctx))
+
+
+def sph_get_tuning(ctx):
+    t, f = ctypes.c_int32(), ctypes.c_double()
+    _check(ctx, lib().sph_get_tuning(ctx, ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
+
+
+def sph_set_profiling(ctx, enable):
+    _check(ctx, lib().sph_set_profiling(ctx, int(bool(enable))))
+
+
+def sph_get_profile(ctx):
+    ms = np.zeros(len(PHASES))
+    ln = np.zeros(len(PHASES), dtype=np.int64)
+    _check(ctx, lib().sph_get_profile(ctx, ctypes.c_void_p(ms.ctypes.data),
+                                      ctypes.c_void_p(ln.ctypes.data), len(PHASES)))
+    return {k: (float(ms[i]), int(ln[i])) for i, k in enumerate(PHASES)}
+
+
+def sph_get_launch_count(ctx):
+    v = ctypes.c_int64()
+    _check(ctx, lib().sph_get_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def sph_get_pair_count(ctx, reset=False):
+    v = ctypes.c_int64()
+    _check(ctx, lib().sph_get_pair_count(ctx, ctypes.byref(v), int(bool(reset))))
+    return v.value
+
+
+# ---- object wrapper -----------------------------------------------------------
+class SPH:
+    """One library context.  Example::
+
+        sim = SPH(max_particles=8000, precision="fp64")
+        sim.set_particles(fields)          # dict of numpy arrays or CUDA tensors
+        sim.step(10)
+        rho = sim.field("rho")
+    """
+
+    def __init__(self, max_particles, precision="mixed", max_patches=1, stream=None, **kw):
+        cfg = sph_config_default()
+        cfg.precision = SPH_FP64 if precision == "fp64" else SPH_MIXED
+        cfg.max_particles = int(max_particles)
+        cfg.max_patches = int(max_patches)
+        if stream is not None:
+            cfg.cuda_stream = stream
+        for k, v in kw.items():
+            if not hasattr(cfg, k):
+                raise TypeError("unknown config field %s" % k)
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.ctx = sph_create(cfg)
+        self.n = 0
+
+    def close(self):
+        if self.ctx:
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, fields):
+        sph_set_particles(self.ctx, fields)
+        self.n = len(fields["x"])
+
+    def set_patches(self, offsets):
+        sph_set_patches(self.ctx, offsets)
+
+    def find_neighbors(self):
+        sph_find_neighbors(self.ctx)
+
+    def neighbors(self, device=None):
+        return sph_copy_neighbors(self.ctx, self.n, device)
+
+    def density(self):
+        sph_density(self.ctx)
+
+    def momentum_energy(self):
+        sph_momentum_energy(self.ctx)
+
+    def step(self, nsteps=1):
+        return sph_step(self.ctx, nsteps)
+
+    def conserved(self, patch=-1):
+        return sph_conserved(self.ctx, patch)
+
+    def field(self, name, out=None):
+        return sph_get_field(self.ctx, name, self.n, out)
+
+    def dt(self, patch=0):
+        return sph_get_dt(self.ctx, patch)
+
+    def get_state(self):
+        return sph_get_state(self.ctx)
+
+    def set_state(self, blob):
+        sph_set_state(self.ctx, blob)
+        import struct
+        self.n = struct.unpack_from("<q", blob, 16)[0]
+
+    def autotune(self):
+        sph_autotune(self.ctx)
+        return sph_get_tuning(self.ctx)
+
+    def profile(self, enable=None):
+        if enable is not None:
+            sph_set_profiling(self.ctx, enable)
+            return None
+        return sph_get_profile(self.ctx)
+
+    def launches(self):
+        return sph_get_launch_count(self.ctx)
+
+    def pair_count(self, reset=False):
+        return sph_get_pair_count(self.ctx, reset)

@@ -1,0 +1,1138 @@
+// sph_api.cu -- the C ABI declared in include/sph.h: context, device memory,
+// the order of the phases of one timestep, CUDA-graph replay, phase timers,
+// checkpoints and the launch autotuner.  All device work is issued on the
+// context's stream; the kernels live in sph_sort.cu, sph_neighbors.cu,
+// sph_pairs.cu and sph_step.cu.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+using namespace sphg;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+bool is_sticky(cudaError_t e)
+{
+    switch (e) {
+    case cudaErrorIllegalAddress:
+    case cudaErrorLaunchFailure:
+    case cudaErrorIllegalInstruction:
+    case cudaErrorMisalignedAddress:
+    case cudaErrorInvalidAddressSpace:
+    case cudaErrorInvalidPc:
+    case cudaErrorHardwareStackError:
+    case cudaErrorAssert:
+    case cudaErrorLaunchTimeout:
+    case cudaErrorECCUncorrectable:
+        return true;
+    default:
+        return false;
+    }
+}
+
+__global__ void k_iota(int64_t n, uint32_t* p)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (uint32_t)i;
+}
+
+__global__ void k_accum_pairs(const uint64_t* total, unsigned long long* acc, const int* status)
+{
+    if (!(*status & kStOverflow)) *acc += *total;
+}
+
+__global__ void k_fill_patch_of(const WorkItem* items, int nitems, uint16_t* patch_of)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        for (int64_t i = w.begin + threadIdx.x; i < w.end; i += blockDim.x) patch_of[i] = (uint16_t)w.patch;
+    }
+}
+
+}  // namespace
+
+struct sph_ctx {
+    sph_config cfg;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 1;
+    std::string err;
+    bool poisoned = false;
+
+    int64_t cap_n = 0, max_pairs = 0, cap_cells = 0;
+    int cap_patch = 0, cap_items = 0;
+    int64_t n = 0;
+    int npatch = 0, nitems = 0, radix_passes = 3;
+    int tpp_nb = 4, tpp_pair = 8;
+    double cell_factor = 0.5;
+    int mixed = 1;
+
+    State st[2];
+    int cur = 0;
+    uint32_t* perm[2] = {nullptr, nullptr};
+    uint16_t* patch_of = nullptr;
+    uint32_t *keys = nullptr, *vals = nullptr, *keys_alt = nullptr, *vals_alt = nullptr;
+    uint32_t *hist = nullptr, *scan32 = nullptr;
+    Grid grid{};
+    Recs rec{};
+    Fp64 f64{};
+    uint32_t *cnt = nullptr, *nown = nullptr, *col = nullptr, *col_plain = nullptr;
+    int64_t col_plain_cap = 0;
+    uint64_t *off = nullptr, *scan64 = nullptr;
+    int64_t scan64_words = 0;
+    PatchDev* pd = nullptr;
+    PatchRed* red = nullptr;
+    WorkItem* items = nullptr;
+    double *partials = nullptr, *cons = nullptr, *scratch = nullptr;
+    int* status = nullptr;
+    int* h_status = nullptr;     // pinned
+    unsigned long long* pair_acc = nullptr;  // sum of |N| over the steps taken
+    std::vector<int64_t> patch_off;
+
+    bool nb_valid = false, rho_valid = false, acc_valid = false;
+    bool fresh = true;           // no sort since set_particles / set_state
+    int64_t nnz = -1;
+
+    bool prof = false;
+    double prof_ms[SPH_PHASE_COUNT] = {};
+    int64_t prof_launch[SPH_PHASE_COUNT] = {};
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    int64_t launches = 0;
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+sph_status fail(sph_ctx* c, sph_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    g_last_error = msg;
+    return s;
+}
+
+sph_status cuda_fail(sph_ctx* c, cudaError_t e, const char* where)
+{
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    if (is_sticky(e)) {
+        if (c) c->poisoned = true;
+        return fail(c, SPH_ESTATE, msg + " (context poisoned)");
+    }
+    return fail(c, SPH_ECUDA, msg);
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+template <typename T>
+bool dalloc(sph_ctx* ctx, T*& p, size_t count)
+{
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return false;
+    }
+    ctx->allocs.push_back(q);
+    p = (T*)q;
+    return true;
+}
+
+Launch launch_of(const sph_ctx* ctx) { return Launch{ctx->stream, ctx->sms}; }
+
+void destroy_graphs(sph_ctx* ctx)
+{
+    for (int k = 0; k < 2; k++) {
+        if (ctx->gexec[k]) cudaGraphExecDestroy(ctx->gexec[k]);
+        ctx->gexec[k] = nullptr;
+        ctx->graph_kernels[k] = 0;
+    }
+}
+
+// ---- phase timers -----------------------------------------------------------
+cudaEvent_t get_event(sph_ctx* ctx)
+{
+    if (!ctx->ev_free.empty()) {
+        cudaEvent_t e = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Phase {
+    sph_ctx* ctx;
+    int ph;
+    cudaEvent_t a = nullptr;
+    int64_t l0;
+    Phase(sph_ctx* c, int p) : ctx(c), ph(p), l0(c->launches)
+    {
+        if (ctx->prof) {
+            a = get_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~Phase()
+    {
+        if (ctx->prof) {
+            cudaEvent_t b = get_event(ctx);
+            cudaEventRecord(b, ctx->stream);
+            ctx->marks.push_back({ph, {a, b}});
+            ctx->prof_launch[ph] += ctx->launches - l0;
+        }
+    }
+};
+
+void collect_profile(sph_ctx* ctx)
+{
+    if (ctx->marks.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& m : ctx->marks) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess)
+            ctx->prof_ms[m.first] += ms;
+        ctx->ev_free.push_back(m.second.first);
+        ctx->ev_free.push_back(m.second.second);
+    }
+    ctx->marks.clear();
+}
+
+// ---- argument bundles ---------------------------------------------------------
+NbArgs nb_args(sph_ctx* ctx)
+{
+    NbArgs a;
+    a.n = ctx->n;
+    a.pd = ctx->pd;
+    a.g = ctx->grid;
+    a.r4 = ctx->rec.r4;
+    const State& s = ctx->st[ctx->cur];
+    a.x = s.x; a.y = s.y; a.z = s.z; a.h = s.h;
+    a.cnt = ctx->cnt;
+    a.nown = ctx->nown;
+    a.off = ctx->off;
+    a.col = ctx->col;
+    a.max_pairs = ctx->max_pairs;
+    a.status = ctx->status;
+    return a;
+}
+
+PairArgs pair_args(sph_ctx* ctx)
+{
+    PairArgs a;
+    a.n = ctx->n;
+    a.pd = ctx->pd;
+    a.patch_of = ctx->patch_of;
+    a.off = ctx->off;
+    a.col = ctx->col;
+    a.s = ctx->st[ctx->cur];
+    a.r = ctx->rec;
+    a.f = ctx->f64;
+    a.gamma = ctx->cfg.gamma;
+    a.alpha = ctx->cfg.av_alpha;
+    a.beta = ctx->cfg.av_beta;
+    a.eps = ctx->cfg.av_eps;
+    a.status = ctx->status;
+    return a;
+}
+
+StepArgs step_args(sph_ctx* ctx)
+{
+    StepArgs a;
+    a.n = ctx->n;
+    a.pd = ctx->pd;
+    a.npatch = ctx->npatch;
+    a.items = ctx->items;
+    a.nitems = ctx->nitems;
+    a.red = ctx->red;
+    a.s = ctx->st[ctx->cur];
+    a.r = ctx->rec;
+    a.f = ctx->f64;
+    a.nown = ctx->nown;
+    a.courant = ctx->cfg.courant;
+    a.dt_growth = ctx->cfg.dt_growth;
+    a.dt_fixed = ctx->cfg.dt_fixed;
+    a.n_target = ctx->cfg.n_target;
+    a.adapt_h = ctx->cfg.adapt_h;
+    a.mixed = ctx->mixed;
+    a.partials = ctx->partials;
+    a.cons = ctx->cons;
+    a.status = ctx->status;
+    return a;
+}
+
+// ---- the phases (asynchronous, no host synchronisation) -----------------------
+void enqueue_sort(sph_ctx* ctx)
+{
+    const Launch L = launch_of(ctx);
+    {
+        Phase p(ctx, SPH_PHASE_BBOX);
+        ctx->launches += launch_reset_red(L, ctx->npatch, ctx->red);
+        ctx->launches += launch_reduce_bbox(L, ctx->st[ctx->cur], ctx->items, ctx->nitems, ctx->red);
+        ctx->launches += launch_grid_params(L, ctx->npatch, ctx->red, ctx->pd, ctx->cell_factor, ctx->status);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_KEYS);
+        ctx->launches += launch_keys(L, ctx->n, ctx->st[ctx->cur], ctx->patch_of, ctx->pd, ctx->keys, ctx->vals);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_SORT);
+        ctx->launches += launch_radix_sort(L, ctx->n, ctx->radix_passes, ctx->keys, ctx->vals, ctx->keys_alt,
+                                           ctx->vals_alt, ctx->hist, ctx->scan32);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_GATHER);
+        cudaMemsetAsync(ctx->grid.cse, 0, (size_t)ctx->cap_cells * sizeof(uint2), ctx->stream);
+        cudaMemsetAsync(ctx->grid.chmax, 0, (size_t)ctx->cap_cells * sizeof(float), ctx->stream);
+        const int nxt = 1 - ctx->cur;
+        ctx->launches += launch_gather(L, ctx->n, ctx->keys, ctx->vals, ctx->st[ctx->cur], ctx->st[nxt],
+                                       ctx->perm[ctx->cur], ctx->perm[nxt], ctx->pd, ctx->grid, ctx->rec,
+                                       ctx->f64, ctx->mixed);
+        ctx->cur = nxt;
+    }
+    ctx->fresh = false;
+}
+
+void enqueue_lists(sph_ctx* ctx)
+{
+    const Launch L = launch_of(ctx);
+    const NbArgs a = nb_args(ctx);
+    {
+        Phase p(ctx, SPH_PHASE_NB_COUNT);
+        ctx->launches += launch_nb_count(L, a, ctx->tpp_nb);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_NB_SCAN);
+        ctx->launches += launch_scan_u32_to_u64(L, ctx->n, ctx->cnt, ctx->off, ctx->scan64, ctx->scan64_words);
+        ctx->launches += launch_check_capacity(L, ctx->off + ctx->n, ctx->max_pairs, ctx->status);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_NB_FILL);
+        ctx->launches += launch_nb_fill(L, a, ctx->tpp_nb);
+    }
+}
+
+void enqueue_density(sph_ctx* ctx)
+{
+    Phase p(ctx, SPH_PHASE_DENSITY);
+    ctx->launches += launch_density(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
+}
+
+void enqueue_momentum(sph_ctx* ctx)
+{
+    Phase p(ctx, SPH_PHASE_MOMENTUM);
+    ctx->launches += launch_momentum(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
+}
+
+void enqueue_step(sph_ctx* ctx)
+{
+    enqueue_sort(ctx);
+    enqueue_lists(ctx);
+    enqueue_density(ctx);
+    const Launch L = launch_of(ctx);
+    {
+        Phase p(ctx, SPH_PHASE_UPDATE);
+        const StepArgs a = step_args(ctx);
+        k_accum_pairs<<<1, 1, 0, ctx->stream>>>(ctx->off + ctx->n, ctx->pair_acc, ctx->status);
+        ctx->launches += 1;
+        ctx->launches += launch_hc_min(L, a);
+        ctx->launches += launch_dt(L, a);
+    }
+    enqueue_momentum(ctx);
+    {
+        Phase p(ctx, SPH_PHASE_UPDATE);
+        const StepArgs a = step_args(ctx);
+        ctx->launches += launch_update(L, a);
+        ctx->launches += launch_step_finalize(L, a);
+    }
+}
+
+sph_status check_status(sph_ctx* ctx, const char* where)
+{
+    cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    collect_profile(ctx);
+    const int st = *ctx->h_status;
+    if (st & kStOverflow)
+        return fail(ctx, SPH_EOVERFLOW, std::string(where) + ": neighbour lists exceed max_pairs");
+    if (st & kStNonFinite) return fail(ctx, SPH_ENONFINITE, std::string(where) + ": non-finite value");
+    if (st & kStTimeout) return fail(ctx, SPH_ETIMEOUT, std::string(where) + ": device wait timed out");
+    return SPH_OK;
+}
+
+sph_status begin_call(sph_ctx* ctx)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    if (ctx->poisoned) return fail(ctx, SPH_ESTATE, "context poisoned by an earlier CUDA error");
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status reset");
+    return SPH_OK;
+}
+
+sph_status after_launches(sph_ctx* ctx, const char* where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    return SPH_OK;
+}
+
+// patch table for the given original-order offsets (slots == original order)
+sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
+{
+    std::vector<PatchDev> pd(np);
+    std::vector<WorkItem> items;
+    int64_t cbase = 0;
+    for (int p = 0; p < np; p++) {
+        PatchDev P;
+        memset(&P, 0, sizeof(P));
+        P.begin = offsets[p];
+        P.end = offsets[p + 1];
+        const int64_t np_ = P.end - P.begin;
+        int64_t cap = 2 * np_ + 4096;
+        const int64_t maxc = (int64_t)kMaxCellsAxis * kMaxCellsAxis * kMaxCellsAxis;
+        if (cap > maxc) cap = maxc;
+        P.cell_base = cbase;
+        P.cell_cap = cap;
+        cbase += cap;
+        P.lz = ctx->cfg.lz;
+        P.item_begin = (int)items.size();
+        for (int64_t b = P.begin; b < P.end; b += kItemChunk) {
+            WorkItem w;
+            w.begin = b;
+            w.end = b + kItemChunk < P.end ? b + kItemChunk : P.end;
+            w.patch = p;
+            w.pad = 0;
+            items.push_back(w);
+        }
+        P.item_end = (int)items.size();
+        pd[p] = P;
+    }
+    if (cbase > ctx->cap_cells || (int)items.size() > ctx->cap_items)
+        return fail(ctx, SPH_EINVAL, "patch table exceeds capacity");
+    CK(cudaMemcpyAsync(ctx->pd, pd.data(), sizeof(PatchDev) * np, cudaMemcpyHostToDevice, ctx->stream));
+    if (!items.empty())
+        CK(cudaMemcpyAsync(ctx->items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    ctx->npatch = np;
+    ctx->nitems = (int)items.size();
+    if (ctx->nitems > 0) {
+        const int grid = ctx->nitems < ctx->sms * 8 ? ctx->nitems : ctx->sms * 8;
+        k_fill_patch_of<<<grid, 256, 0, ctx->stream>>>(ctx->items, ctx->nitems, ctx->patch_of);
+    }
+    int bits = 0;
+    while ((1 << bits) < np) bits++;
+    ctx->radix_passes = (kPatchShift + bits + 7) / 8;
+    ctx->patch_off.assign(offsets, offsets + np + 1);
+    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
+    destroy_graphs(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return after_launches(ctx, "setup_patches");
+}
+
+double* state_field(State& s, int k)
+{
+    double* f[13] = {s.x, s.y, s.z, s.vx, s.vy, s.vz, s.m, s.h, s.u, s.du_prev, s.axp, s.ayp, s.azp};
+    return f[k];
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void sph_config_default(sph_config* c)
+{
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->precision = SPH_MIXED;
+    c->kernel = SPH_KERNEL_WENDLAND;
+    c->gamma = 5.0 / 3.0;
+    c->n_target = 100.0;
+    c->courant = 0.2;
+    c->dt_growth = 1.1;
+    c->av_alpha = 1.0;
+    c->av_beta = 2.0;
+    c->av_eps = 0.01;
+    c->lz = 1.0;
+    c->dt_fixed = 0.0;
+    c->adapt_h = 1;
+    c->threads_per_particle = 0;
+    c->cell_factor = 0.5;
+    c->max_particles = 1 << 20;
+    c->max_pairs = 0;
+    c->max_patches = 1;
+    c->use_graph = 0;
+    c->cuda_stream = nullptr;
+}
+
+const char* sph_status_string(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "SPH_OK";
+    case SPH_EINVAL: return "SPH_EINVAL";
+    case SPH_ENOMEM: return "SPH_ENOMEM";
+    case SPH_ECUDA: return "SPH_ECUDA";
+    case SPH_EOVERFLOW: return "SPH_EOVERFLOW";
+    case SPH_ENONFINITE: return "SPH_ENONFINITE";
+    case SPH_ETIMEOUT: return "SPH_ETIMEOUT";
+    case SPH_ESTATE: return "SPH_ESTATE";
+    }
+    return "unknown";
+}
+
+const char* sph_last_error(const sph_ctx* ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_last_error.c_str();
+}
+
+void sph_destroy(sph_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    destroy_graphs(ctx);
+    for (auto& m : ctx->marks) {
+        cudaEventDestroy(m.second.first);
+        cudaEventDestroy(m.second.second);
+    }
+    for (auto e : ctx->ev_free) cudaEventDestroy(e);
+    for (void* p : ctx->allocs)
+        if (p) cudaFree(p);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
+{
+    if (!out) return fail(nullptr, SPH_EINVAL, "out is NULL");
+    *out = nullptr;
+    sph_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else sph_config_default(&cfg);
+    if (cfg.precision != SPH_FP64 && cfg.precision != SPH_MIXED)
+        return fail(nullptr, SPH_EINVAL, "precision must be SPH_FP64 or SPH_MIXED");
+    if (cfg.kernel != SPH_KERNEL_WENDLAND) return fail(nullptr, SPH_EINVAL, "unsupported kernel");
+    if (cfg.max_particles < 1 || cfg.max_particles > kMaxParticles)
+        return fail(nullptr, SPH_EINVAL, "max_particles must be in [1, 2^25]");
+    if (cfg.max_patches < 1 || cfg.max_patches > kMaxPatches)
+        return fail(nullptr, SPH_EINVAL, "max_patches must be in [1, 256]");
+    if (cfg.cell_factor == 0.0) cfg.cell_factor = 0.5;
+    if (!(cfg.cell_factor >= 0.5 && cfg.cell_factor <= 4.0))
+        return fail(nullptr, SPH_EINVAL, "cell_factor must be in [0.5, 4]");
+    const int t = cfg.threads_per_particle;
+    if (!(t == 0 || t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32))
+        return fail(nullptr, SPH_EINVAL, "threads_per_particle must be 0, 1, 2, 4, 8, 16 or 32");
+    if (!(cfg.gamma > 1.0) || !(cfg.courant > 0.0) || !(cfg.dt_growth >= 1.0) || !(cfg.lz > 0.0) ||
+        !(cfg.n_target > 0.0) || !(cfg.av_alpha >= 0.0) || !(cfg.av_beta >= 0.0) || !(cfg.av_eps > 0.0) ||
+        !(cfg.dt_fixed >= 0.0))
+        return fail(nullptr, SPH_EINVAL, "invalid physical parameter");
+    if (cfg.max_pairs < 0) return fail(nullptr, SPH_EINVAL, "max_pairs < 0");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(nullptr, SPH_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    sph_ctx* ctx = new (std::nothrow) sph_ctx();
+    if (!ctx) return fail(nullptr, SPH_ENOMEM, "host allocation failed");
+    ctx->cfg = cfg;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cfg.cuda_stream) {
+        ctx->stream = (cudaStream_t)cfg.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, SPH_ECUDA, "stream creation failed");
+        }
+        ctx->own_stream = true;
+    }
+    ctx->mixed = cfg.precision == SPH_MIXED;
+    ctx->cell_factor = cfg.cell_factor;
+    if (t) ctx->tpp_nb = ctx->tpp_pair = t;
+    ctx->cap_n = cfg.max_particles;
+    ctx->cap_patch = cfg.max_patches;
+    ctx->max_pairs = cfg.max_pairs > 0 ? cfg.max_pairs : 160 * cfg.max_particles;
+    ctx->cap_items = (int)(ctx->cap_n / kItemChunk + ctx->cap_patch + 1);
+    ctx->cap_cells = 2 * ctx->cap_n + (int64_t)4096 * ctx->cap_patch;
+    const size_t N = (size_t)ctx->cap_n;
+
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; b++) {
+        State& s = ctx->st[b];
+        double** f[13] = {&s.x, &s.y, &s.z, &s.vx, &s.vy, &s.vz, &s.m, &s.h, &s.u, &s.du_prev, &s.axp, &s.ayp, &s.azp};
+        for (int k = 0; k < 13 && ok; k++) ok = dalloc(ctx, *f[k], N);
+        ok = ok && dalloc(ctx, ctx->perm[b], N);
+    }
+    ok = ok && dalloc(ctx, ctx->patch_of, N);
+    ok = ok && dalloc(ctx, ctx->keys, N) && dalloc(ctx, ctx->vals, N) && dalloc(ctx, ctx->keys_alt, N) &&
+         dalloc(ctx, ctx->vals_alt, N);
+    const size_t hw = radix_hist_words(ctx->cap_n);
+    ok = ok && dalloc(ctx, ctx->hist, hw) && dalloc(ctx, ctx->scan32, (size_t)scan_tmp_words((int64_t)hw));
+    uint2* cse = nullptr;
+    float* chmax = nullptr;
+    uint32_t* cellxyz = nullptr;
+    ok = ok && dalloc(ctx, cse, (size_t)ctx->cap_cells) && dalloc(ctx, chmax, (size_t)ctx->cap_cells) &&
+         dalloc(ctx, cellxyz, N);
+    ctx->grid.cse = cse;
+    ctx->grid.chmax = chmax;
+    ctx->grid.cellxyz = cellxyz;
+    ok = ok && dalloc(ctx, ctx->rec.r4, N);
+    if (ctx->mixed) {
+        ok = ok && dalloc(ctx, ctx->rec.r5, N) && dalloc(ctx, ctx->rec.rv, N) && dalloc(ctx, ctx->rec.rt, N) &&
+             dalloc(ctx, ctx->rec.hc, N) && dalloc(ctx, ctx->rec.pf, N) && dalloc(ctx, ctx->rec.acc, N);
+    } else {
+        Fp64& f = ctx->f64;
+        double** g[14] = {&f.vhx, &f.vhy, &f.vhz, &f.rho, &f.P, &f.c, &f.A, &f.hc, &f.invh, &f.ax, &f.ay, &f.az, &f.du, nullptr};
+        for (int k = 0; k < 13 && ok; k++) ok = dalloc(ctx, *g[k], N);
+    }
+    ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->nown, N) && dalloc(ctx, ctx->off, N + 1) &&
+         dalloc(ctx, ctx->col, (size_t)ctx->max_pairs);
+    ctx->scan64_words = scan_tmp_words(ctx->cap_n);
+    ok = ok && dalloc(ctx, ctx->scan64, (size_t)ctx->scan64_words);
+    ok = ok && dalloc(ctx, ctx->pd, (size_t)ctx->cap_patch) && dalloc(ctx, ctx->red, (size_t)ctx->cap_patch) &&
+         dalloc(ctx, ctx->items, (size_t)ctx->cap_items) && dalloc(ctx, ctx->partials, (size_t)ctx->cap_items * 7) &&
+         dalloc(ctx, ctx->cons, (size_t)ctx->cap_patch * 7) && dalloc(ctx, ctx->scratch, N) &&
+         dalloc(ctx, ctx->status, 1) && dalloc(ctx, ctx->pair_acc, 1);
+    ctx->grid.patch_of = ctx->patch_of;
+    if (ok && cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) ok = false;
+    if (!ok) {
+        sph_destroy(ctx);
+        return fail(nullptr, SPH_ENOMEM, "device allocation failed for the requested capacities");
+    }
+    cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+    cudaMemsetAsync(ctx->pair_acc, 0, sizeof(unsigned long long), ctx->stream);
+    int64_t zero_off[2] = {0, 0};
+    sph_status s = setup_patches(ctx, 1, zero_off);
+    if (s != SPH_OK) {
+        std::string m = ctx->err;
+        sph_destroy(ctx);
+        return fail(nullptr, s, m);
+    }
+    *out = ctx;
+    return SPH_OK;
+}
+
+sph_status sph_set_particles(sph_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                             const double* vx, const double* vy, const double* vz, const double* m,
+                             const double* h, const double* u, int on_device)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (n < 0 || n > ctx->cap_n) return fail(ctx, SPH_EINVAL, "n out of range [0, max_particles]");
+    const double* src[9] = {x, y, z, vx, vy, vz, m, h, u};
+    if (n > 0)
+        for (int k = 0; k < 9; k++)
+            if (!src[k]) return fail(ctx, SPH_EINVAL, "NULL field pointer");
+    ctx->cur = 0;
+    State& s = ctx->st[0];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int k = 0; k < 9; k++)
+        if (n > 0) CK(cudaMemcpyAsync(state_field(s, k), src[k], (size_t)n * 8, kind, ctx->stream));
+    for (int k = 9; k < 13; k++) CK(cudaMemsetAsync(state_field(s, k), 0, (size_t)(n > 0 ? n : 1) * 8, ctx->stream));
+    ctx->n = n;
+    if (n > 0) {
+        const int grid = (int)((n + 255) / 256 < ctx->sms * 16 ? (n + 255) / 256 : ctx->sms * 16);
+        k_iota<<<grid, 256, 0, ctx->stream>>>(n, ctx->perm[0]);
+        launch_validate(launch_of(ctx), n, s, ctx->status);
+    }
+    int64_t offs[2] = {0, n};
+    st = setup_patches(ctx, 1, offs);
+    if (st != SPH_OK) return st;
+    ctx->fresh = true;
+    ctx->nnz = -1;
+    st = check_status(ctx, "sph_set_particles");
+    if (st == SPH_ENONFINITE)
+        return fail(ctx, SPH_EINVAL, "sph_set_particles: inputs must be finite with m > 0 and h > 0");
+    return st;
+}
+
+sph_status sph_set_patches(sph_ctx* ctx, int32_t n_patches, const int64_t* offsets)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!ctx->fresh) return fail(ctx, SPH_ESTATE, "sph_set_patches must follow sph_set_particles");
+    if (n_patches < 1 || n_patches > ctx->cap_patch || !offsets)
+        return fail(ctx, SPH_EINVAL, "n_patches out of range or offsets NULL");
+    if (offsets[0] != 0 || offsets[n_patches] != ctx->n) return fail(ctx, SPH_EINVAL, "offsets must span [0, n]");
+    for (int p = 0; p < n_patches; p++)
+        if (offsets[p + 1] < offsets[p]) return fail(ctx, SPH_EINVAL, "offsets must be non-decreasing");
+    return setup_patches(ctx, n_patches, offsets);
+}
+
+sph_status sph_find_neighbors(sph_ctx* ctx)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
+    destroy_graphs(ctx);
+    enqueue_sort(ctx);
+    enqueue_lists(ctx);
+    st = after_launches(ctx, "sph_find_neighbors");
+    if (st != SPH_OK) return st;
+    uint64_t nnz = 0;
+    CK(cudaMemcpyAsync(&nnz, ctx->off + ctx->n, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    st = check_status(ctx, "sph_find_neighbors");
+    ctx->nnz = (int64_t)nnz;
+    if (st != SPH_OK) return st;
+    ctx->nb_valid = true;
+    return SPH_OK;
+}
+
+sph_status sph_get_neighbors(sph_ctx* ctx, const uint64_t** off, const uint32_t** col, const uint32_t** perm,
+                             int64_t* nnz)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!ctx->nb_valid) return fail(ctx, SPH_ESTATE, "no current neighbour lists");
+    if (col) {
+        if (ctx->col_plain_cap < ctx->nnz) {
+            if (ctx->col_plain) {
+                for (auto& q : ctx->allocs)
+                    if (q == (void*)ctx->col_plain) q = nullptr;
+                cudaFree(ctx->col_plain);
+                ctx->col_plain = nullptr;
+                ctx->col_plain_cap = 0;
+            }
+            uint32_t* p = nullptr;
+            if (!dalloc(ctx, p, (size_t)(ctx->nnz > 0 ? ctx->nnz : 1)))
+                return fail(ctx, SPH_ENOMEM, "column buffer allocation failed");
+            ctx->col_plain = p;
+            ctx->col_plain_cap = ctx->nnz;
+        }
+        ctx->launches += launch_unpack_cols(launch_of(ctx), ctx->nnz, ctx->col, ctx->col_plain);
+        CK(cudaStreamSynchronize(ctx->stream));
+        *col = ctx->col_plain;
+    }
+    if (off) *off = ctx->off;
+    if (perm) *perm = ctx->perm[ctx->cur];
+    if (nnz) *nnz = ctx->nnz;
+    return after_launches(ctx, "sph_get_neighbors");
+}
+
+sph_status sph_copy_neighbors(sph_ctx* ctx, uint64_t* off, uint32_t* col, uint32_t* perm, int on_device)
+{
+    const uint64_t* o = nullptr;
+    const uint32_t *c = nullptr, *pm = nullptr;
+    int64_t nnz = 0;
+    sph_status st = sph_get_neighbors(ctx, &o, col ? &c : nullptr, &pm, &nnz);
+    if (st != SPH_OK) return st;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (off) CK(cudaMemcpyAsync(off, o, sizeof(uint64_t) * (ctx->n + 1), k, ctx->stream));
+    if (col && nnz > 0) CK(cudaMemcpyAsync(col, c, sizeof(uint32_t) * nnz, k, ctx->stream));
+    if (perm && ctx->n > 0) CK(cudaMemcpyAsync(perm, pm, sizeof(uint32_t) * ctx->n, k, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SPH_OK;
+}
+
+sph_status sph_density(sph_ctx* ctx)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!ctx->nb_valid) return fail(ctx, SPH_ESTATE, "sph_density needs current neighbour lists");
+    enqueue_density(ctx);
+    st = after_launches(ctx, "sph_density");
+    if (st != SPH_OK) return st;
+    st = check_status(ctx, "sph_density");
+    ctx->rho_valid = st == SPH_OK;
+    ctx->acc_valid = false;
+    return st;
+}
+
+sph_status sph_momentum_energy(sph_ctx* ctx)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!ctx->rho_valid) return fail(ctx, SPH_ESTATE, "sph_momentum_energy needs sph_density first");
+    enqueue_momentum(ctx);
+    st = after_launches(ctx, "sph_momentum_energy");
+    if (st != SPH_OK) return st;
+    st = check_status(ctx, "sph_momentum_energy");
+    ctx->acc_valid = st == SPH_OK;
+    return st;
+}
+
+sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (nsteps < 0) return fail(ctx, SPH_EINVAL, "nsteps < 0");
+    if (ctx->n == 0) return SPH_OK;
+    const bool graph = ctx->cfg.use_graph && !ctx->prof;
+    for (int k = 0; k < nsteps; k++) {
+        if (graph) {
+            const int par = ctx->cur;
+            if (!ctx->gexec[par]) {
+                cudaGraph_t g = nullptr;
+                const int64_t l0 = ctx->launches;
+                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                enqueue_step(ctx);
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+                ctx->cur = par;
+                ctx->launches = l0;
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+                int64_t nk = 0;
+                size_t nn = 0;
+                cudaGraphGetNodes(g, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                cudaGraphGetNodes(g, nodes.data(), &nn);
+                for (auto nd : nodes) {
+                    cudaGraphNodeType ty;
+                    cudaGraphNodeGetType(nd, &ty);
+                    if (ty == cudaGraphNodeTypeKernel) nk++;
+                }
+                e = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+                ctx->graph_kernels[par] = nk;
+            }
+            CK(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
+            ctx->launches += ctx->graph_kernels[par];
+            ctx->cur = 1 - par;
+            ctx->fresh = false;
+        } else {
+            enqueue_step(ctx);
+        }
+    }
+    st = after_launches(ctx, "sph_step");
+    if (st != SPH_OK) return st;
+    st = check_status(ctx, "sph_step");
+    ctx->nb_valid = false;
+    ctx->rho_valid = ctx->acc_valid = (st == SPH_OK);
+    if (st != SPH_OK) return st;
+    if (dt_last) {
+        CK(cudaMemcpy(dt_last, &ctx->pd[0].dt, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return SPH_OK;
+}
+
+sph_status sph_conserved(sph_ctx* ctx, int32_t patch, double out[7])
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!out || patch < -1 || patch >= ctx->npatch) return fail(ctx, SPH_EINVAL, "bad patch or out");
+    const StepArgs a = step_args(ctx);
+    ctx->launches += launch_conserved_items(launch_of(ctx), a);
+    ctx->launches += launch_conserved_finalize(launch_of(ctx), a);
+    st = after_launches(ctx, "sph_conserved");
+    if (st != SPH_OK) return st;
+    std::vector<double> c((size_t)ctx->npatch * 7);
+    CK(cudaMemcpyAsync(c.data(), ctx->cons, sizeof(double) * c.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (patch >= 0) {
+        for (int q = 0; q < 7; q++) out[q] = c[(size_t)patch * 7 + q];
+    } else {
+        for (int q = 0; q < 7; q++) {
+            double s = 0.0, comp = 0.0;
+            for (int p = 0; p < ctx->npatch; p++) {
+                const double v = c[(size_t)p * 7 + q];
+                const double t = s + v;
+                if (fabs(s) >= fabs(v)) comp += (s - t) + v;
+                else comp += (v - t) + s;
+                s = t;
+            }
+            out[q] = s + comp;
+        }
+    }
+    return SPH_OK;
+}
+
+sph_status sph_get_field(sph_ctx* ctx, int32_t field, double* dst, int on_device)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (field < 0 || field >= SPH_FIELD_COUNT) return fail(ctx, SPH_EINVAL, "unknown field");
+    if (!dst && ctx->n > 0) return fail(ctx, SPH_EINVAL, "dst is NULL");
+    if (ctx->n == 0) return SPH_OK;
+    const Launch L = launch_of(ctx);
+    double* out = on_device ? dst : ctx->scratch;
+    const uint32_t* perm = ctx->perm[ctx->cur];
+    const int64_t n = ctx->n;
+    if (field <= SPH_FIELD_AZP) {
+        ctx->launches += launch_unpermute_f64(L, n, state_field(ctx->st[ctx->cur], field), perm, out);
+    } else if (field <= SPH_FIELD_C) {
+        if (!ctx->rho_valid) return fail(ctx, SPH_ESTATE, "density not computed for the current order");
+        if (ctx->mixed) {
+            if (field == SPH_FIELD_P) ctx->launches += launch_unpermute_f32(L, n, ctx->rec.pf, 1, perm, out);
+            else ctx->launches += launch_unpermute_f32(L, n, (const float*)ctx->rec.rt + (field == SPH_FIELD_RHO ? 0 : 2),
+                                                       4, perm, out);
+        } else {
+            const double* s = field == SPH_FIELD_RHO ? ctx->f64.rho : (field == SPH_FIELD_P ? ctx->f64.P : ctx->f64.c);
+            ctx->launches += launch_unpermute_f64(L, n, s, perm, out);
+        }
+    } else if (field <= SPH_FIELD_DU) {
+        if (!ctx->acc_valid) return fail(ctx, SPH_ESTATE, "accelerations not computed for the current order");
+        const int k = field - SPH_FIELD_AX;
+        if (ctx->mixed) {
+            ctx->launches += launch_unpermute_f32(L, n, (const float*)ctx->rec.acc + k, 4, perm, out);
+        } else {
+            const double* s[4] = {ctx->f64.ax, ctx->f64.ay, ctx->f64.az, ctx->f64.du};
+            ctx->launches += launch_unpermute_f64(L, n, s[k], perm, out);
+        }
+    } else if (field == SPH_FIELD_NOWN) {
+        if (ctx->fresh) return fail(ctx, SPH_ESTATE, "no neighbour search yet");
+        ctx->launches += launch_unpermute_u32(L, n, ctx->nown, perm, out);
+    } else {
+        if (ctx->fresh) return fail(ctx, SPH_ESTATE, "no neighbour search yet");
+        ctx->launches += launch_row_lengths(L, n, ctx->off, perm, out);
+    }
+    st = after_launches(ctx, "sph_get_field");
+    if (st != SPH_OK) return st;
+    if (!on_device) CK(cudaMemcpyAsync(dst, out, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SPH_OK;
+}
+
+sph_status sph_get_dt(sph_ctx* ctx, int32_t patch, double* dt, double* dt_prev, int64_t* step)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (patch < 0 || patch >= ctx->npatch) return fail(ctx, SPH_EINVAL, "bad patch");
+    PatchDev P;
+    CK(cudaMemcpyAsync(&P, ctx->pd + patch, sizeof(P), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dt) *dt = P.dt;
+    if (dt_prev) *dt_prev = P.dt_prev;
+    if (step) *step = P.step;
+    return SPH_OK;
+}
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    int64_t version, n, npatch, reserved;
+};
+}  // namespace
+
+sph_status sph_get_state(sph_ctx* ctx, void* buf, size_t* bytes)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!bytes) return fail(ctx, SPH_EINVAL, "bytes is NULL");
+    const int64_t n = ctx->n, np = ctx->npatch;
+    const size_t need = sizeof(StateHeader) + sizeof(int64_t) * (np + 1) + sizeof(double) * 3 * np +
+                        sizeof(uint32_t) * n + sizeof(double) * 13 * n;
+    if (!buf) {
+        *bytes = need;
+        return SPH_OK;
+    }
+    if (*bytes < need) return fail(ctx, SPH_EINVAL, "buffer too small");
+    char* p = (char*)buf;
+    StateHeader h;
+    memcpy(h.magic, "SPHGB300", 8);
+    h.version = 1;
+    h.n = n;
+    h.npatch = np;
+    h.reserved = 0;
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    memcpy(p, ctx->patch_off.data(), sizeof(int64_t) * (np + 1));
+    p += sizeof(int64_t) * (np + 1);
+    std::vector<PatchDev> pd(np);
+    CK(cudaMemcpyAsync(pd.data(), ctx->pd, sizeof(PatchDev) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q < np; q++) {
+        double t[3] = {pd[q].dt, pd[q].dt_prev, (double)pd[q].step};
+        memcpy(p, t, sizeof(t));
+        p += sizeof(t);
+    }
+    if (n > 0) {
+        CK(cudaMemcpy(p, ctx->perm[ctx->cur], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+        p += sizeof(uint32_t) * n;
+        for (int k = 0; k < 13; k++) {
+            CK(cudaMemcpy(p, state_field(ctx->st[ctx->cur], k), sizeof(double) * n, cudaMemcpyDeviceToHost));
+            p += sizeof(double) * n;
+        }
+    }
+    *bytes = need;
+    return SPH_OK;
+}
+
+sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (!buf || bytes < sizeof(StateHeader)) return fail(ctx, SPH_EINVAL, "bad state buffer");
+    const char* p = (const char*)buf;
+    StateHeader h;
+    memcpy(&h, p, sizeof(h));
+    p += sizeof(h);
+    if (memcmp(h.magic, "SPHGB300", 8) != 0 || h.version != 1) return fail(ctx, SPH_EINVAL, "not a state buffer");
+    const int64_t n = h.n, np = h.npatch;
+    if (n < 0 || n > ctx->cap_n || np < 1 || np > ctx->cap_patch) return fail(ctx, SPH_EINVAL, "state exceeds capacity");
+    const size_t need = sizeof(StateHeader) + sizeof(int64_t) * (np + 1) + sizeof(double) * 3 * np +
+                        sizeof(uint32_t) * n + sizeof(double) * 13 * n;
+    if (bytes < need) return fail(ctx, SPH_EINVAL, "state buffer truncated");
+    std::vector<int64_t> offs(np + 1);
+    memcpy(offs.data(), p, sizeof(int64_t) * (np + 1));
+    p += sizeof(int64_t) * (np + 1);
+    std::vector<double> times(3 * np);
+    memcpy(times.data(), p, sizeof(double) * 3 * np);
+    p += sizeof(double) * 3 * np;
+    ctx->cur = 0;
+    ctx->n = n;
+    if (n > 0) {
+        CK(cudaMemcpy(ctx->perm[0], p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+        p += sizeof(uint32_t) * n;
+        for (int k = 0; k < 13; k++) {
+            CK(cudaMemcpy(state_field(ctx->st[0], k), p, sizeof(double) * n, cudaMemcpyHostToDevice));
+            p += sizeof(double) * n;
+        }
+    }
+    st = setup_patches(ctx, (int)np, offs.data());
+    if (st != SPH_OK) return st;
+    std::vector<PatchDev> pd(np);
+    CK(cudaMemcpy(pd.data(), ctx->pd, sizeof(PatchDev) * np, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < np; q++) {
+        pd[q].dt = times[3 * q];
+        pd[q].dt_prev = times[3 * q + 1];
+        pd[q].step = (int64_t)times[3 * q + 2];
+    }
+    CK(cudaMemcpy(ctx->pd, pd.data(), sizeof(PatchDev) * np, cudaMemcpyHostToDevice));
+    ctx->fresh = true;
+    ctx->nnz = -1;
+    return SPH_OK;
+}
+
+sph_status sph_autotune(sph_ctx* ctx)
+{
+    sph_status st = begin_call(ctx);
+    if (st != SPH_OK) return st;
+    if (ctx->n == 0) return SPH_OK;
+    const bool prof0 = ctx->prof;
+    ctx->prof = false;
+    destroy_graphs(ctx);
+    const double factors[3] = {0.5, 0.75, 1.0};
+    const int tpps[4] = {2, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timeit = [&](auto&& fn) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            cudaEventRecord(e0, ctx->stream);
+            fn();
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) best = ms;
+        }
+        return best;
+    };
+    double best_total = 1e300, best_f = ctx->cell_factor;
+    int best_nb = ctx->tpp_nb, best_pair = ctx->tpp_pair;
+    for (double f : factors) {
+        ctx->cell_factor = f;
+        enqueue_sort(ctx);
+        float bnb = 1e30f, bpair = 1e30f;
+        int tnb = 4, tpair = 8;
+        for (int t : tpps) {
+            ctx->tpp_nb = t;
+            float ms = timeit([&] { enqueue_lists(ctx); });
+            if (ms < bnb) { bnb = ms; tnb = t; }
+        }
+        ctx->tpp_nb = tnb;
+        enqueue_lists(ctx);
+        for (int t : tpps) {
+            ctx->tpp_pair = t;
+            float ms = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
+            if (ms < bpair) { bpair = ms; tpair = t; }
+        }
+        const double tot = (double)bnb + (double)bpair;
+        if (tot < best_total) {
+            best_total = tot;
+            best_f = f;
+            best_nb = tnb;
+            best_pair = tpair;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->cell_factor = best_f;
+    ctx->tpp_nb = best_nb;
+    ctx->tpp_pair = best_pair;
+    ctx->prof = prof0;
+    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
+    st = after_launches(ctx, "sph_autotune");
+    if (st != SPH_OK) return st;
+    return check_status(ctx, "sph_autotune");
+}
+
+sph_status sph_get_tuning(sph_ctx* ctx, int32_t* tpp, double* cell_factor)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    if (tpp) *tpp = ctx->tpp_pair;
+    if (cell_factor) *cell_factor = ctx->cell_factor;
+    return SPH_OK;
+}
+
+sph_status sph_set_profiling(sph_ctx* ctx, int enable)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    ctx->prof = enable != 0;
+    return SPH_OK;
+}
+
+sph_status sph_get_profile(sph_ctx* ctx, double* ms, int64_t* launches, int32_t nphase)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    collect_profile(ctx);
+    for (int k = 0; k < nphase && k < SPH_PHASE_COUNT; k++) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->prof_launch[k];
+    }
+    for (int k = 0; k < SPH_PHASE_COUNT; k++) {
+        ctx->prof_ms[k] = 0.0;
+        ctx->prof_launch[k] = 0;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_get_launch_count(sph_ctx* ctx, int64_t* launches)
+{
+    if (!ctx || !launches) return fail(ctx, SPH_EINVAL, "null argument");
+    *launches = ctx->launches;
+    return SPH_OK;
+}
+
+sph_status sph_get_pair_count(sph_ctx* ctx, int64_t* total, int reset)
+{
+    if (!ctx || !total) return fail(ctx, SPH_EINVAL, "null argument");
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, ctx->pair_acc, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *total = (int64_t)v;
+    if (reset) CK(cudaMemsetAsync(ctx->pair_acc, 0, sizeof(v), ctx->stream));
+    return SPH_OK;
+}
+
+sph_status sph_get_nnz(sph_ctx* ctx, int64_t* nnz)
+{
+    if (!ctx || !nnz) return fail(ctx, SPH_EINVAL, "null argument");
+    *nnz = ctx->nnz;
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// sph_internal.cuh -- device data layout and launch declarations shared by
+// the CUDA translation units of libsph_gb300.so.  Not part of the C ABI.
+//
+// Particles live in HBM as structure-of-arrays, sorted by (patch, Morton
+// cell).  Per patch, a uniform grid of cells with edge s >= 2 h_max *
+// cell_factor covers the bounding box in x, y and the period lz in z; a
+// particle searches the (2K+1)^3 cells around its own (K = 1 for
+// cell_factor >= 1, K = 2 below), pruned by each cell's largest h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/sph.h"
+
+namespace sphg {
+
+constexpr int kMortonBits = 8;                 // per axis: at most 256 cells
+constexpr int kMaxCellsAxis = 1 << kMortonBits;
+constexpr int kPatchShift = 3 * kMortonBits;   // key = patch << 24 | morton
+constexpr int kColBits = 25;                   // packed column: j | stencil << 25
+constexpr uint32_t kColMask = (1u << kColBits) - 1u;
+constexpr int64_t kMaxParticles = int64_t(1) << kColBits;
+constexpr int kMaxPatches = 256;
+constexpr int kItemChunk = 4096;               // particles per work item
+constexpr int kStencilCells = 125;             // (2K+1)^3 for K <= 2
+
+// status word bits (device, sticky until the host clears it)
+constexpr int kStOverflow = 1;
+constexpr int kStNonFinite = 2;
+constexpr int kStTimeout = 4;
+
+// Guard band of the FP32 neighbour pre-filter: a candidate is decided in FP32
+// only when r^2 is outside [T (1 - tol), T (1 + tol)], T the FP64 threshold;
+// otherwise the exact FP64 predicate decides.  tol = 2^-13 + 2^-19 s/h_i
+// bounds the FP32 rounding of the cell-relative r^2 (error ~ 12 * 2^-24 s/h
+// relative to T) with a margin of more than 2x.
+constexpr float kTolBase = 1.0f / 8192.0f;
+constexpr float kTolCell = 1.0f / 524288.0f;
+// Cell edges carry a relative margin so that FP32 cell assignment can never
+// separate two particles closer than 2 h_max by more than K cells.
+constexpr double kCellMargin = 1.0 + 1.0 / 1024.0;
+
+struct PatchDev {
+    int64_t begin, end;          // sorted slot range (fixed after set_patches)
+    int64_t cell_base, cell_cap; // slice of the cell tables
+    int32_t item_begin, item_end;  // work items of this patch
+    double xmin, ymin, s, sz, hmax, lz;
+    float s_f, sz_f, lz_f, inv_s_f, inv_sz_f, hmax_f;
+    int32_t ncx, ncy, ncz, K;
+    int32_t zmode;               // 0: 2K+1 distinct z cells; 1: all z cells + float wrap
+    int32_t pad;
+    // time state
+    double dt, dt_prev;
+    int64_t step;
+};
+
+// Per-patch reduction slots, ordered-integer encoded doubles.
+struct PatchRed {
+    unsigned long long xmin, ymin, xmax, ymax, hmax, hcmin;
+};
+
+struct WorkItem {
+    int64_t begin, end;
+    int32_t patch, pad;
+};
+
+// Device views handed to the kernels.
+struct State {
+    double *x, *y, *z, *vx, *vy, *vz, *m, *h, *u, *du_prev, *axp, *ayp, *azp;
+};
+
+struct Grid {
+    uint2* cse;          // [cell] (start, end) in sorted order, 0/0 = empty
+    float* chmax;        // [cell] largest h (FP32) in the cell
+    uint32_t* cellxyz;   // [particle] cx | cy << 8 | cz << 16
+    const uint16_t* patch_of;  // [particle] patch index
+};
+
+struct Recs {             // FP32 records (written by gather / density)
+    float4* r4;          // {ox, oy, oz, h}      neighbour pre-filter
+    float4* r5;          // {ox, oy, oz, m}      pair sums (mixed)
+    float4* rv;          // {vhx, vhy, vhz, 1/(2h)} time-centred velocity (mixed)
+    float4* rt;          // {rho, P/rho^2, c, h} thermodynamics (mixed)
+    float* hc;           // h/c (mixed)
+    float* pf;           // P (mixed)
+    float4* acc;         // {ax, ay, az, du} (mixed)
+};
+
+struct Fp64 {             // FP64-path fields
+    double *vhx, *vhy, *vhz;   // time-centred velocity
+    double *rho, *P, *c, *A, *hc, *invh;
+    double *ax, *ay, *az, *du;
+};
+
+// ---- small device helpers ------------------------------------------------
+__device__ __forceinline__ unsigned long long ord_f64(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ __forceinline__ double unord_f64(unsigned long long u)
+{
+    unsigned long long b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+#endif
+}
+__host__ __device__ __forceinline__ uint32_t part1by2(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t compact1by2(uint32_t v)
+{
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030C30C3u;
+    v = (v | (v >> 4)) & 0x0300F00Fu;
+    v = (v | (v >> 8)) & 0x030000FFu;
+    v = (v | (v >> 16)) & 0x000003FFu;
+    return v;
+}
+
+// ---- launch wrappers (each returns the number of kernels launched) --------
+struct Launch {
+    cudaStream_t stream;
+    int sms;
+};
+
+int launch_reduce_bbox(const Launch& L, const State& s, const WorkItem* items, int nitems,
+                       PatchRed* red);
+int launch_grid_params(const Launch& L, int npatch, const PatchRed* red, PatchDev* pd,
+                       double cell_factor, int* status);
+int launch_keys(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of,
+                const PatchDev* pd, uint32_t* keys, uint32_t* vals);
+// LSD radix sort of (keys, vals); result in (keys, vals); uses alternates.
+int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, uint32_t* vals,
+                      uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist, uint32_t* scan_tmp);
+size_t radix_hist_words(int64_t n);
+int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint32_t* svals,
+                  const State& src, const State& dst, const uint32_t* perm_src,
+                  uint32_t* perm_dst, const PatchDev* pd, const Grid& g, const Recs& r,
+                  const Fp64& f, int mixed);
+// exclusive scan of n u32 counts into u64 offsets[n+1]; total -> offsets[n]
+int launch_scan_u32_to_u64(const Launch& L, int64_t n, const uint32_t* in, uint64_t* out,
+                           uint64_t* tmp, int64_t tmp_words);
+int64_t scan_tmp_words(int64_t n);
+
+struct NbArgs {
+    int64_t n;
+    const PatchDev* pd;
+    Grid g;
+    const float4* r4;
+    const double *x, *y, *z, *h;
+    uint32_t* cnt;
+    uint32_t* nown;
+    const uint64_t* off;
+    uint32_t* col;
+    int64_t max_pairs;
+    int* status;
+};
+int launch_nb_count(const Launch& L, const NbArgs& a, int tpp);
+int launch_nb_fill(const Launch& L, const NbArgs& a, int tpp);
+int launch_check_capacity(const Launch& L, const uint64_t* total, int64_t max_pairs, int* status);
+int launch_unpack_cols(const Launch& L, int64_t nnz, const uint32_t* col, uint32_t* out);
+
+struct PairArgs {
+    int64_t n;
+    const PatchDev* pd;
+    const uint16_t* patch_of;
+    const uint64_t* off;
+    const uint32_t* col;
+    State s;
+    Recs r;
+    Fp64 f;
+    double gamma, alpha, beta, eps;
+    int* status;
+};
+int launch_density(const Launch& L, const PairArgs& a, int tpp, int mixed);
+int launch_momentum(const Launch& L, const PairArgs& a, int tpp, int mixed);
+
+struct StepArgs {
+    int64_t n;
+    PatchDev* pd;
+    int npatch;
+    const WorkItem* items;
+    int nitems;
+    PatchRed* red;
+    State s;
+    Recs r;
+    Fp64 f;
+    const uint32_t* nown;
+    double courant, dt_growth, dt_fixed, n_target;
+    int adapt_h, mixed;
+    double* partials;    // [nitems][7]
+    double* cons;        // [npatch][7]
+    int* status;
+};
+int launch_hc_min(const Launch& L, const StepArgs& a);
+int launch_dt(const Launch& L, const StepArgs& a);
+int launch_update(const Launch& L, const StepArgs& a);
+int launch_conserved_items(const Launch& L, const StepArgs& a);
+int launch_conserved_finalize(const Launch& L, const StepArgs& a);
+int launch_step_finalize(const Launch& L, const StepArgs& a);
+int launch_unpermute_f64(const Launch& L, int64_t n, const double* src, const uint32_t* perm,
+                         double* dst);
+int launch_unpermute_f32(const Launch& L, int64_t n, const float* src, int stride,
+                         const uint32_t* perm, double* dst);
+int launch_unpermute_u32(const Launch& L, int64_t n, const uint32_t* src, const uint32_t* perm,
+                         double* dst);
+int launch_row_lengths(const Launch& L, int64_t n, const uint64_t* off, const uint32_t* perm,
+                       double* dst);
+int launch_validate(const Launch& L, int64_t n, const State& s, int* status);
+int launch_reset_red(const Launch& L, int npatch, PatchRed* red);
+
+}  // namespace sphg

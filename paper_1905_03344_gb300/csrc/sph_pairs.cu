@@ -1,0 +1,375 @@
+// sph_pairs.cu -- the SPH pair sums over the CSR neighbour lists (Sec. 3):
+//   density  rho_i = m_i W(0, h_i) + sum_j m_j W(r_ij, h_i)        (R1, Eq. 2)
+//   EOS      P = (gamma - 1) rho u,  c = sqrt(gamma P / rho)        (R9)
+//   momentum a_i  = -sum_j m_j (A_i + A_j + Pi_ij) grad_i Wbar_ij   (R4)
+//   energy   du_i =  sum_j m_j (A_i + Pi_ij / 2) v_ij . grad_i Wbar_ij (R6)
+// with A = P / rho^2, Wbar_ij = (W(r,h_i) + W(r,h_j)) / 2 and the Monaghan
+// viscosity Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar for approaching
+// pairs, mu = hbar v_ij . x_ij / (r^2 + eps hbar^2) (R5).
+//
+// Wendland kernel (Eq. 2, 1/h^3 restored): with w = 1/(2h) and
+// q = 1 - r w = 1 - v/2,
+//   W(r, h)         = sigma/h^3 q^4 (5 - 4 q)          (2v + 1 = 5 - 4q)
+//   grad_i W(r, h)  = -160 sigma w^5 q^3 (x_i - x_j)   (5 sigma / h^5 = 160 sigma w^5)
+// so grad_i Wbar_ij = -80 sigma (w_i^5 q_i^3 + w_j^5 q_j^3) (x_i - x_j), and the
+// factor 80 sigma = 105/pi is applied once per particle.
+//
+// One group of TPP lanes per particle strides over the particle's row; the
+// group reduces its partial sums with shuffles.  Mixed precision: positions
+// are FP32 offsets from the particle's cell origin, the column word carries
+// the stencil cell so x_i - x_j = (o_i - o_j) - dc s exactly up to FP32
+// rounding of o; sums are Kahan-compensated FP32.  FP64 path: every pair
+// operation in double.
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+constexpr double kSigmaW = 21.0 / (16.0 * 3.14159265358979323846);
+constexpr float kSigmaWf = (float)kSigmaW;
+constexpr float k80Sigma = (float)(80.0 * kSigmaW);
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v)
+{
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// merge another lane's compensated sum (value s2 - c2) into (s, c)
+__device__ __forceinline__ void kahan_merge(float& s, float& c, float s2, float c2)
+{
+    kahan_add(s, c, s2);
+    kahan_add(s, c, -c2);
+}
+
+template <int TPP>
+__device__ __forceinline__ void group_kahan_reduce(float& s, float& c, unsigned gmask)
+{
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(gmask, s, o);
+        const float c2 = __shfl_xor_sync(gmask, c, o);
+        kahan_merge(s, c, s2, c2);
+    }
+}
+
+template <int TPP>
+__device__ __forceinline__ double group_sum(double v, unsigned gmask)
+{
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+    return v;
+}
+
+// stencil offsets of the packed column word: {dcx, dcy, dcz, t}, the z entry
+// used with zmode 0, t (z cell offset, FP32 minimum image) with zmode 1
+__device__ __forceinline__ void fill_stencil_table(float4* tab)
+{
+    for (int k = threadIdx.x; k < kStencilCells; k += blockDim.x) {
+        const int zd = k / 25;
+        tab[k] = make_float4((float)(k % 5 - 2), (float)((k / 5) % 5 - 2), (float)(zd - 2), (float)zd);
+    }
+    __syncthreads();
+}
+
+struct GroupIdx {
+    int gl;
+    unsigned gmask;
+};
+
+template <int TPP>
+__device__ __forceinline__ GroupIdx group_idx()
+{
+    const int lane = threadIdx.x & 31;
+    GroupIdx g;
+    g.gl = lane & (TPP - 1);
+    g.gmask = TPP == 32 ? 0xffffffffu : (((1u << TPP) - 1u) << (lane & ~(TPP - 1)));
+    return g;
+}
+
+// pair separation x_i - x_j from cell-relative FP32 coordinates
+__device__ __forceinline__ void rel_dx(const float4& e, int zmode, float s_f, float sz_f, float lz_f,
+                                       float oxi, float oyi, float ozi, const float4& q, float& dx,
+                                       float& dy, float& dz)
+{
+    dx = fmaf(-e.x, s_f, oxi - q.x);
+    dy = fmaf(-e.y, s_f, oyi - q.y);
+    dz = fmaf(-(zmode ? e.w : e.z), sz_f, ozi - q.z);
+    if (zmode) {
+        if (dz > 0.5f * lz_f) dz -= lz_f;
+        else if (dz < -0.5f * lz_f) dz += lz_f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A5 + A6, mixed precision
+// ---------------------------------------------------------------------------
+template <int TPP>
+__global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
+{
+    __shared__ float4 tab[kStencilCells];
+    fill_stencil_table(tab);
+    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    const GroupIdx G = group_idx<TPP>();
+    const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
+    const float gam = (float)a.gamma;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+        const PatchDev* P = a.pd + a.patch_of[i];
+        const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
+        const int zmode = P->zmode;
+        const float4 ri = a.r.r5[i];
+        const float hf = a.r.r4[i].w;
+        const float inv2h = 0.5f / hf;
+        const uint64_t b = a.off[i], e = a.off[i + 1];
+        float sum = 0.0f, comp = 0.0f;
+        for (uint64_t k = b + G.gl; k < e; k += TPP) {
+            const uint32_t cw = a.col[k];
+            const float4 q = a.r.r5[cw & kColMask];
+            const float4 st = tab[cw >> kColBits];
+            float dx, dy, dz;
+            rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(r2 + 1e-30f);
+            const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
+            const float q2 = qv * qv;
+            kahan_add(sum, comp, q.w * (q2 * q2 * fmaf(-4.0f, qv, 5.0f)));
+        }
+        group_kahan_reduce<TPP>(sum, comp, G.gmask);
+        if (G.gl == 0) {
+            const float tot = (float)((double)ri.w + ((double)sum - (double)comp));
+            const float rho = kSigmaWf * tot / (hf * hf * hf);
+            const float u = (float)a.s.u[i];
+            const float Pr = (gam - 1.0f) * rho * u;
+            const float c = sqrtf(gam * Pr / rho);
+            const float A = Pr / (rho * rho);
+            a.r.rt[i] = make_float4(rho, A, c, hf);
+            a.r.pf[i] = Pr;
+            a.r.hc[i] = hf / c;
+            if (!(rho > 0.0f) || !isfinite(rho) || !isfinite(Pr) || !isfinite(c))
+                atomicOr(a.status, kStNonFinite);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A5 + A6, FP64
+// ---------------------------------------------------------------------------
+template <int TPP>
+__global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
+{
+    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    const GroupIdx G = group_idx<TPP>();
+    const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+        const PatchDev* P = a.pd + a.patch_of[i];
+        const double lz = P->lz, hl = 0.5 * P->lz;
+        const double xi = a.s.x[i], yi = a.s.y[i], zi = a.s.z[i], hi = a.s.h[i];
+        const double w = 0.5 * a.f.invh[i];
+        const uint64_t b = a.off[i], e = a.off[i + 1];
+        double sum = 0.0;
+        for (uint64_t k = b + G.gl; k < e; k += TPP) {
+            const uint32_t j = a.col[k] & kColMask;
+            const double dx = xi - a.s.x[j], dy = yi - a.s.y[j];
+            double dz = zi - a.s.z[j];
+            if (dz > hl) dz -= lz;
+            else if (dz < -hl) dz += lz;
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            const double qv = fmax(1.0 - r * w, 0.0);
+            const double q2 = qv * qv;
+            sum += a.s.m[j] * (q2 * q2 * (5.0 - 4.0 * qv));
+        }
+        sum = group_sum<TPP>(sum, G.gmask);
+        if (G.gl == 0) {
+            const double rho = kSigmaW * (a.s.m[i] + sum) / (hi * hi * hi);
+            const double Pr = (a.gamma - 1.0) * rho * a.s.u[i];
+            const double c = sqrt(a.gamma * Pr / rho);
+            a.f.rho[i] = rho;
+            a.f.P[i] = Pr;
+            a.f.c[i] = c;
+            a.f.A[i] = Pr / (rho * rho);
+            a.f.hc[i] = hi / c;
+            if (!(rho > 0.0) || !isfinite(rho) || !isfinite(Pr) || !isfinite(c))
+                atomicOr(a.status, kStNonFinite);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A7, mixed precision
+// ---------------------------------------------------------------------------
+template <int TPP>
+__global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
+{
+    __shared__ float4 tab[kStencilCells];
+    fill_stencil_table(tab);
+    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    const GroupIdx G = group_idx<TPP>();
+    const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
+    const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+        const PatchDev* P = a.pd + a.patch_of[i];
+        const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
+        const int zmode = P->zmode;
+        const float4 ri = a.r.r5[i];
+        const float4 vi = a.r.rv[i];
+        const float4 ti = a.r.rt[i];
+        const float wi = vi.w;
+        const float wi2 = wi * wi;
+        const float wi5 = wi2 * wi2 * wi;
+        const uint64_t b = a.off[i], e = a.off[i + 1];
+        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f;
+        for (uint64_t k = b + G.gl; k < e; k += TPP) {
+            const uint32_t cw = a.col[k];
+            const uint32_t j = cw & kColMask;
+            const float4 q = a.r.r5[j];
+            const float4 vj = a.r.rv[j];
+            const float4 tj = a.r.rt[j];
+            const float4 st = tab[cw >> kColBits];
+            float dx, dy, dz;
+            rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(r2 + 1e-30f);
+            const float qi = fmaxf(fmaf(-r, wi, 1.0f), 0.0f);
+            const float qj = fmaxf(fmaf(-r, vj.w, 1.0f), 0.0f);
+            const float wj2 = vj.w * vj.w;
+            const float wj5 = wj2 * wj2 * vj.w;
+            const float F = fmaf(wj5, qj * qj * qj, wi5 * (qi * qi * qi));
+            const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+            const float vdot = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+            const float hbar = 0.5f * (ti.w + tj.w);
+            const float mu = __fdividef(hbar * vdot, fmaf(eps * hbar, hbar, r2));
+            const float pi_ = vdot < 0.0f
+                                  ? __fdividef(mu * fmaf(beta, mu, -alpha * 0.5f * (ti.z + tj.z)),
+                                               0.5f * (ti.x + tj.x))
+                                  : 0.0f;
+            const float g = q.w * F;
+            const float fa = g * (ti.y + tj.y + pi_);
+            kahan_add(sx, cx, fa * dx);
+            kahan_add(sy, cy, fa * dy);
+            kahan_add(sz, cz, fa * dz);
+            kahan_add(su, cu, -g * fmaf(0.5f, pi_, ti.y) * vdot);
+        }
+        group_kahan_reduce<TPP>(sx, cx, G.gmask);
+        group_kahan_reduce<TPP>(sy, cy, G.gmask);
+        group_kahan_reduce<TPP>(sz, cz, G.gmask);
+        group_kahan_reduce<TPP>(su, cu, G.gmask);
+        if (G.gl == 0) {
+            const float4 r = make_float4(k80Sigma * (float)((double)sx - (double)cx),
+                                         k80Sigma * (float)((double)sy - (double)cy),
+                                         k80Sigma * (float)((double)sz - (double)cz),
+                                         k80Sigma * (float)((double)su - (double)cu));
+            a.r.acc[i] = r;
+            if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(r.z) || !isfinite(r.w))
+                atomicOr(a.status, kStNonFinite);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A7, FP64
+// ---------------------------------------------------------------------------
+template <int TPP>
+__global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
+{
+    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    const GroupIdx G = group_idx<TPP>();
+    const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
+    const double S80 = 80.0 * kSigmaW;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+        const PatchDev* P = a.pd + a.patch_of[i];
+        const double lz = P->lz, hl = 0.5 * P->lz;
+        const double xi = a.s.x[i], yi = a.s.y[i], zi = a.s.z[i];
+        const double vxi = a.f.vhx[i], vyi = a.f.vhy[i], vzi = a.f.vhz[i];
+        const double hi = a.s.h[i], wi = 0.5 * a.f.invh[i];
+        const double wi5 = wi * wi * wi * wi * wi;
+        const double rhoi = a.f.rho[i], Ai = a.f.A[i], ci = a.f.c[i];
+        const uint64_t b = a.off[i], e = a.off[i + 1];
+        double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0;
+        for (uint64_t k = b + G.gl; k < e; k += TPP) {
+            const uint32_t j = a.col[k] & kColMask;
+            const double dx = xi - a.s.x[j], dy = yi - a.s.y[j];
+            double dz = zi - a.s.z[j];
+            if (dz > hl) dz -= lz;
+            else if (dz < -hl) dz += lz;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double r = sqrt(r2);
+            const double wj = 0.5 * a.f.invh[j];
+            const double qi = fmax(1.0 - r * wi, 0.0);
+            const double qj = fmax(1.0 - r * wj, 0.0);
+            const double F = wi5 * qi * qi * qi + wj * wj * wj * wj * wj * qj * qj * qj;
+            const double vx = vxi - a.f.vhx[j], vy = vyi - a.f.vhy[j], vz = vzi - a.f.vhz[j];
+            const double vdot = vx * dx + vy * dy + vz * dz;
+            double pi_ = 0.0;
+            if (vdot < 0.0) {
+                const double hbar = 0.5 * (hi + a.s.h[j]);
+                const double mu = hbar * vdot / (r2 + a.eps * hbar * hbar);
+                pi_ = (-a.alpha * 0.5 * (ci + a.f.c[j]) * mu + a.beta * mu * mu) /
+                      (0.5 * (rhoi + a.f.rho[j]));
+            }
+            const double g = a.s.m[j] * F;
+            const double fa = g * (Ai + a.f.A[j] + pi_);
+            ax += fa * dx;
+            ay += fa * dy;
+            az += fa * dz;
+            du -= g * (Ai + 0.5 * pi_) * vdot;
+        }
+        ax = group_sum<TPP>(ax, G.gmask);
+        ay = group_sum<TPP>(ay, G.gmask);
+        az = group_sum<TPP>(az, G.gmask);
+        du = group_sum<TPP>(du, G.gmask);
+        if (G.gl == 0) {
+            a.f.ax[i] = S80 * ax;
+            a.f.ay[i] = S80 * ay;
+            a.f.az[i] = S80 * az;
+            a.f.du[i] = S80 * du;
+            if (!isfinite(ax) || !isfinite(ay) || !isfinite(az) || !isfinite(du))
+                atomicOr(a.status, kStNonFinite);
+        }
+    }
+}
+
+#define SPH_DISPATCH_TPP(KERNEL, tpp, blocks, L, a)                                   \
+    switch (tpp) {                                                                    \
+    case 1: KERNEL<1><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 2: KERNEL<2><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 4: KERNEL<4><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 16: KERNEL<16><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
+    case 32: KERNEL<32><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
+    default: KERNEL<8><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;         \
+    }
+
+static int64_t pair_blocks(const Launch& L, int64_t n, int tpp)
+{
+    int64_t blocks = (n * tpp + 255) / 256;
+    const int64_t cap = (int64_t)L.sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return blocks;
+}
+
+int launch_density(const Launch& L, const PairArgs& a, int tpp, int mixed)
+{
+    if (a.n <= 0) return 0;
+    const int64_t blocks = pair_blocks(L, a.n, tpp);
+    if (mixed) {
+        SPH_DISPATCH_TPP(k_density_mixed, tpp, blocks, L, a);
+    } else {
+        SPH_DISPATCH_TPP(k_density_fp64, tpp, blocks, L, a);
+    }
+    return 1;
+}
+
+int launch_momentum(const Launch& L, const PairArgs& a, int tpp, int mixed)
+{
+    if (a.n <= 0) return 0;
+    const int64_t blocks = pair_blocks(L, a.n, tpp);
+    if (mixed) {
+        SPH_DISPATCH_TPP(k_momentum_mixed, tpp, blocks, L, a);
+    } else {
+        SPH_DISPATCH_TPP(k_momentum_fp64, tpp, blocks, L, a);
+    }
+    return 1;
+}
+
+}  // namespace sphg

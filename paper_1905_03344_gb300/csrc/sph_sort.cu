@@ -1,0 +1,541 @@
+// sph_sort.cu -- neighbour discovery, first half (Table 1 "Neighbour
+// Discovery"; the paper's tree walk is replaced by a Morton-ordered cell
+// grid): per-patch bounding box and largest h (FP64, ordered-integer
+// atomics), grid parameters, Morton cell keys, a stable LSD radix sort of
+// (key, slot), and the gather of every particle field into the sorted order,
+// which also writes the cell table and the FP32 cell-relative records.
+// Also the device-wide exclusive scan used by the radix sort and the CSR.
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+static inline int blocks_for(int64_t work, int threads, int sms, int per_sm)
+{
+    int64_t b = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)sms * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b)
+{
+    return a < b ? a : b;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+// ---------------------------------------------------------------------------
+// A1a: per-patch min/max of x, y and max of h; one block per work item (a
+// chunk of one patch), one atomic per block and value.  Min/max are exact,
+// so the result does not depend on the order of the atomics.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_reduce_bbox(State s, const WorkItem* items, int nitems,
+                                                     PatchRed* red)
+{
+    __shared__ unsigned long long sh[5][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        unsigned long long v[5] = {~0ull, ~0ull, 0ull, 0ull, 0ull};
+        for (int64_t i = w.begin + threadIdx.x; i < w.end; i += blockDim.x) {
+            unsigned long long a = ord_f64(s.x[i]), b = ord_f64(s.y[i]), c = ord_f64(s.h[i]);
+            v[0] = umin64(v[0], a);
+            v[1] = umin64(v[1], b);
+            v[2] = umax64(v[2], a);
+            v[3] = umax64(v[3], b);
+            v[4] = umax64(v[4], c);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            v[0] = umin64(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+            v[1] = umin64(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+            v[2] = umax64(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
+            v[3] = umax64(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+            v[4] = umax64(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
+        }
+        if (lane == 0)
+            for (int q = 0; q < 5; q++) sh[q][warp] = v[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nw = blockDim.x >> 5;
+            for (int ww = 1; ww < nw; ww++) {
+                v[0] = umin64(v[0], sh[0][ww]);
+                v[1] = umin64(v[1], sh[1][ww]);
+                v[2] = umax64(v[2], sh[2][ww]);
+                v[3] = umax64(v[3], sh[3][ww]);
+                v[4] = umax64(v[4], sh[4][ww]);
+            }
+            PatchRed* r = red + w.patch;
+            atomicMin(&r->xmin, v[0]);
+            atomicMin(&r->ymin, v[1]);
+            atomicMax(&r->xmax, v[2]);
+            atomicMax(&r->ymax, v[3]);
+            atomicMax(&r->hmax, v[4]);
+        }
+        __syncthreads();
+    }
+}
+
+int launch_reduce_bbox(const Launch& L, const State& s, const WorkItem* items, int nitems,
+                       PatchRed* red)
+{
+    if (nitems <= 0) return 0;
+    int grid = nitems < L.sms * 8 ? nitems : L.sms * 8;
+    k_reduce_bbox<<<grid, 256, 0, L.stream>>>(s, items, nitems, red);
+    return 1;
+}
+
+__global__ void k_reset_red(int npatch, PatchRed* red)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < npatch) {
+        red[p].xmin = ~0ull;
+        red[p].ymin = ~0ull;
+        red[p].xmax = 0ull;
+        red[p].ymax = 0ull;
+        red[p].hmax = 0ull;
+        red[p].hcmin = ~0ull;
+    }
+}
+
+int launch_reset_red(const Launch& L, int npatch, PatchRed* red)
+{
+    k_reset_red<<<(npatch + 255) / 256, 256, 0, L.stream>>>(npatch, red);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// A1b: grid of each patch.  Cell edge s = 2 h_max cell_factor (with margin),
+// K = 1 stencil half-extent for cell_factor >= 1, else 2, so K s >= 2 h_max.
+// At most 256 cells per axis and cell_cap cells per patch (s grows if not).
+// Along z: ncz = floor(lz / s) cells of edge lz / ncz; when fewer than 2K+1,
+// every z cell is visited once and the minimum image is taken in FP32.
+// ---------------------------------------------------------------------------
+__global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, double cell_factor,
+                              int* status)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npatch) return;
+    PatchDev P = pd[p];
+    const int K = cell_factor >= 1.0 ? 1 : 2;
+    double xmin = 0, ymin = 0, xmax = 0, ymax = 0, hmax = 0;
+    if (P.end > P.begin) {
+        xmin = unord_f64(red[p].xmin);
+        ymin = unord_f64(red[p].ymin);
+        xmax = unord_f64(red[p].xmax);
+        ymax = unord_f64(red[p].ymax);
+        hmax = unord_f64(red[p].hmax);
+    }
+    double ex = xmax - xmin, ey = ymax - ymin;
+    if (!isfinite(ex) || !isfinite(ey) || !isfinite(hmax) || !isfinite(xmin) || !isfinite(ymin)) {
+        // non-finite positions: flag, and keep a one-cell grid so that every
+        // index computed from it stays inside the cell table
+        atomicOr(status, kStNonFinite);
+        xmin = ymin = 0.0;
+        ex = ey = 0.0;
+        hmax = 0.0;
+    }
+    double s = 2.0 * hmax * cell_factor * kCellMargin;
+    const double sext = fmax(ex, ey) / (double)(kMaxCellsAxis - 1) * kCellMargin;
+    if (s < sext) s = sext;
+    if (!(s > 0.0)) s = P.lz > 0.0 ? P.lz : 1.0;
+    int64_t ncx = 1, ncy = 1, ncz = 1;
+    for (int iter = 0; iter < 200; iter++) {
+        ncx = (int64_t)floor(ex / s) + 1;
+        ncy = (int64_t)floor(ey / s) + 1;
+        ncz = (int64_t)floor(P.lz / s);
+        if (ncz < 1) ncz = 1;
+        if (ncz > kMaxCellsAxis) ncz = kMaxCellsAxis;
+        if (ncx <= kMaxCellsAxis && ncy <= kMaxCellsAxis && ncx * ncy * ncz <= P.cell_cap) break;
+        s *= 1.25;
+    }
+    if (!(ncx >= 1 && ncy >= 1 && ncx <= kMaxCellsAxis && ncy <= kMaxCellsAxis &&
+          ncx * ncy * ncz <= P.cell_cap)) {
+        atomicOr(status, kStNonFinite);
+        ncx = ncy = ncz = 1;
+    }
+    P.xmin = xmin;
+    P.ymin = ymin;
+    P.hmax = hmax;
+    P.s = s;
+    P.sz = P.lz / (double)ncz;
+    P.ncx = (int)ncx;
+    P.ncy = (int)ncy;
+    P.ncz = (int)ncz;
+    P.K = K;
+    P.zmode = ncz >= 2 * K + 1 ? 0 : 1;
+    P.s_f = (float)s;
+    P.sz_f = (float)P.sz;
+    P.lz_f = (float)P.lz;
+    P.inv_s_f = (float)(1.0 / s);
+    P.inv_sz_f = (float)(1.0 / P.sz);
+    P.hmax_f = (float)hmax;
+    pd[p] = P;
+}
+
+int launch_grid_params(const Launch& L, int npatch, const PatchRed* red, PatchDev* pd,
+                       double cell_factor, int* status)
+{
+    k_grid_params<<<(npatch + 127) / 128, 128, 0, L.stream>>>(npatch, red, pd, cell_factor, status);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// A1c: key = patch << 24 | Morton(cx, cy, cz), cell coordinates in FP32 from
+// the FP64 offset to the grid origin (error < 1e-4 cell, inside the margin).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_keys(int64_t n, State s, const uint16_t* patch_of,
+                                              const PatchDev* pd, uint32_t* keys, uint32_t* vals)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = patch_of[i];
+        const PatchDev* P = pd + p;
+        const float tx = (float)(s.x[i] - P->xmin) * P->inv_s_f;
+        const float ty = (float)(s.y[i] - P->ymin) * P->inv_s_f;
+        const float tz = (float)(s.z[i] + 0.5 * P->lz) * P->inv_sz_f;
+        int cx = (int)floorf(tx), cy = (int)floorf(ty), cz = (int)floorf(tz);
+        cx = min(max(cx, 0), P->ncx - 1);
+        cy = min(max(cy, 0), P->ncy - 1);
+        cz = min(max(cz, 0), P->ncz - 1);
+        keys[i] = ((uint32_t)p << kPatchShift) | part1by2((uint32_t)cx) |
+                  (part1by2((uint32_t)cy) << 1) | (part1by2((uint32_t)cz) << 2);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+int launch_keys(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of,
+                const PatchDev* pd, uint32_t* keys, uint32_t* vals)
+{
+    if (n <= 0) return 0;
+    k_keys<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, s, patch_of, pd, keys, vals);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan helpers (blockDim.x a multiple of 32, <= 1024).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// returns the exclusive prefix of v over the block; *total receives the sum
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* total, T* sh /* >= 33 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? sh[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    T res = inc - v + sh[warp];
+    *total = sh[32];
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan, reduce-then-scan in three launches.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Tin* in, int64_t n, Tout* part)
+{
+    __shared__ Tout sh[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    Tout v = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) v += (Tout)in[i];
+    }
+    Tout tot;
+    block_excl_scan<Tout>(v, &tot, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <typename Tout>
+__global__ void __launch_bounds__(1024) k_scan_spine(Tout* part, int64_t nb)
+{
+    __shared__ Tout sh[33];
+    Tout carry = 0;
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        Tout v = i < nb ? part[i] : Tout(0);
+        Tout tot;
+        Tout ex = block_excl_scan<Tout>(v, &tot, sh);
+        if (i < nb) part[i] = ex + carry;
+        carry += tot;
+    }
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* in, int64_t n, const Tout* part,
+                                                           Tout* out, int write_total)
+{
+    __shared__ Tout sh[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    Tout loc[kScanItems];
+    Tout sum = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k;
+        Tout v = i < n ? (Tout)in[i] : Tout(0);
+        loc[k] = sum;
+        sum += v;
+    }
+    Tout tot;
+    Tout ex = block_excl_scan<Tout>(sum, &tot, sh) + part[blockIdx.x];
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k;
+        if (i < n) out[i] = ex + loc[k];
+    }
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[blockIdx.x] + tot;
+}
+
+int64_t scan_tmp_words(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+int launch_scan_u32_to_u64(const Launch& L, int64_t n, const uint32_t* in, uint64_t* out,
+                           uint64_t* tmp, int64_t tmp_words)
+{
+    (void)tmp_words;
+    if (n <= 0) {
+        cudaMemsetAsync(out, 0, sizeof(uint64_t), L.stream);
+        return 0;
+    }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_reduce<uint32_t, uint64_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp);
+    k_scan_spine<uint64_t><<<1, 1024, 0, L.stream>>>(tmp, nb);
+    k_scan_down<uint32_t, uint64_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp, out, 1);
+    return 3;
+}
+
+static int scan_u32(const Launch& L, int64_t n, const uint32_t* in, uint32_t* out, uint32_t* tmp)
+{
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_reduce<uint32_t, uint32_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp);
+    k_scan_spine<uint32_t><<<1, 1024, 0, L.stream>>>(tmp, nb);
+    k_scan_down<uint32_t, uint32_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp, out, 0);
+    return 3;
+}
+
+// ---------------------------------------------------------------------------
+// A2: stable LSD radix sort, 8-bit digits.  Per pass: a digit histogram per
+// tile of 4096 keys (digit-major), an exclusive scan of the histograms, and a
+// scatter that ranks keys stably inside the tile (warp match + per-warp
+// counters, warps in tile order), stages the tile in shared memory in digit
+// order and writes each digit run contiguously.
+// ---------------------------------------------------------------------------
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsStrips = 16;
+constexpr int kRsTile = kRsWarps * 32 * kRsStrips;  // 4096
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint32_t* keys, int64_t n, int shift,
+                                                       uint32_t* hist, int ntiles)
+{
+    __shared__ uint32_t sh[256];
+    const int lane = threadIdx.x & 31;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        sh[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = (int64_t)tile * kRsTile;
+        for (int k = threadIdx.x; k < kRsTile; k += blockDim.x) {
+            const int64_t i = base + k;
+            const uint32_t d = i < n ? ((keys[i] >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&sh[d], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        hist[(int64_t)threadIdx.x * ntiles + tile] = sh[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint32_t* kin, const uint32_t* vin,
+                                                          int64_t n, int shift, const uint32_t* hoff,
+                                                          int ntiles, uint32_t* kout, uint32_t* vout)
+{
+    __shared__ uint32_t s_keys[kRsTile];
+    __shared__ uint32_t s_vals[kRsTile];
+    __shared__ uint32_t s_wcnt[kRsWarps][256];
+    __shared__ uint32_t s_dstart[256];
+    __shared__ uint32_t s_goff[256];
+    __shared__ uint32_t s_scan[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int k = threadIdx.x; k < kRsWarps * 256; k += blockDim.x) (&s_wcnt[0][0])[k] = 0;
+        __syncthreads();
+        uint32_t kr[kRsStrips], vr[kRsStrips];
+        uint16_t pr[kRsStrips];
+        const int64_t wbase = (int64_t)tile * kRsTile + (int64_t)warp * 32 * kRsStrips;
+#pragma unroll
+        for (int t = 0; t < kRsStrips; t++) {
+            const int64_t i = wbase + t * 32 + lane;
+            const bool valid = i < n;
+            const uint32_t key = valid ? kin[i] : 0xffffffffu;
+            const uint32_t val = valid ? vin[i] : 0u;
+            const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            uint32_t before = 0;
+            if (valid) before = s_wcnt[warp][d];
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) s_wcnt[warp][d] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            kr[t] = key;
+            vr[t] = val;
+            pr[t] = (uint16_t)(before + rank);
+        }
+        __syncthreads();
+        {   // per digit: exclusive offsets of the warps, then digit starts in the tile
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int w = 0; w < kRsWarps; w++) {
+                uint32_t c = s_wcnt[w][d];
+                s_wcnt[w][d] = run;
+                run += c;
+            }
+            uint32_t tot;
+            s_dstart[d] = block_excl_scan<uint32_t>(run, &tot, s_scan);
+            s_goff[d] = hoff[(int64_t)d * ntiles + tile];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kRsStrips; t++) {
+            const int64_t i = wbase + t * 32 + lane;
+            if (i < n) {
+                const uint32_t d = (kr[t] >> shift) & 255u;
+                const uint32_t lp = s_dstart[d] + s_wcnt[warp][d] + pr[t];
+                s_keys[lp] = kr[t];
+                s_vals[lp] = vr[t];
+            }
+        }
+        __syncthreads();
+        const int64_t rem = n - (int64_t)tile * kRsTile;
+        const int tn = rem < kRsTile ? (int)rem : kRsTile;
+        for (int k = threadIdx.x; k < tn; k += blockDim.x) {
+            const uint32_t key = s_keys[k];
+            const uint32_t d = (key >> shift) & 255u;
+            const uint32_t g = s_goff[d] + ((uint32_t)k - s_dstart[d]);
+            kout[g] = key;
+            vout[g] = s_vals[k];
+        }
+        __syncthreads();
+    }
+}
+
+size_t radix_hist_words(int64_t n)
+{
+    int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+    if (ntiles < 1) ntiles = 1;
+    return (size_t)(256 * ntiles);
+}
+
+int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, uint32_t* vals,
+                      uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist, uint32_t* scan_tmp)
+{
+    if (n <= 1) return 0;
+    const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
+    const int grid = ntiles < L.sms * 4 ? ntiles : L.sms * 4;
+    const int64_t nh = (int64_t)256 * ntiles;
+    int launches = 0;
+    uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+    for (int ps = 0; ps < passes; ps++) {
+        const int shift = 8 * ps;
+        k_rs_hist<<<grid, kRsThreads, 0, L.stream>>>(ki, n, shift, hist, ntiles);
+        launches += 1 + scan_u32(L, nh, hist, hist, scan_tmp);
+        k_rs_scatter<<<grid, kRsThreads, 0, L.stream>>>(ki, vi, n, shift, hist, ntiles, ko, vo);
+        launches++;
+        uint32_t* t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    if (ki != keys) {   // odd number of passes: copy back
+        cudaMemcpyAsync(keys, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, L.stream);
+        cudaMemcpyAsync(vals, vi, (size_t)n * 4, cudaMemcpyDeviceToDevice, L.stream);
+    }
+    return launches;
+}
+
+// ---------------------------------------------------------------------------
+// A2b/A3: gather every field into sorted order, write the permutation, the
+// cell table (start/end by key boundaries, largest h per cell) and the FP32
+// records with positions relative to the particle's cell origin.  Also forms
+// the time-centred velocity v_{n-1/2} + a_{n-1} dt_{n-1}/2 used by the
+// viscosity and the energy equation.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys, const uint32_t* svals,
+                                                State src, State dst, const uint32_t* perm_src,
+                                                uint32_t* perm_dst, const PatchDev* pd, Grid g,
+                                                Recs r, Fp64 f, int mixed)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = skeys[k];
+        const uint32_t si = svals[k];
+        const PatchDev* P = pd + (key >> kPatchShift);
+        const double x = src.x[si], y = src.y[si], z = src.z[si];
+        const double vx = src.vx[si], vy = src.vy[si], vz = src.vz[si];
+        const double m = src.m[si], h = src.h[si];
+        const double axp = src.axp[si], ayp = src.ayp[si], azp = src.azp[si];
+        dst.x[k] = x; dst.y[k] = y; dst.z[k] = z;
+        dst.vx[k] = vx; dst.vy[k] = vy; dst.vz[k] = vz;
+        dst.m[k] = m; dst.h[k] = h;
+        dst.u[k] = src.u[si];
+        dst.du_prev[k] = src.du_prev[si];
+        dst.axp[k] = axp; dst.ayp[k] = ayp; dst.azp[k] = azp;
+        perm_dst[k] = perm_src[si];
+
+        const uint32_t mort = key & ((1u << kPatchShift) - 1u);
+        const uint32_t cx = compact1by2(mort), cy = compact1by2(mort >> 1), cz = compact1by2(mort >> 2);
+        g.cellxyz[k] = cx | (cy << 8) | (cz << 16);
+        const float ox = (float)(x - (P->xmin + (double)cx * P->s));
+        const float oy = (float)(y - (P->ymin + (double)cy * P->s));
+        const float oz = (float)(z - (-0.5 * P->lz + (double)cz * P->sz));
+        const float hf = (float)h;
+        r.r4[k] = make_float4(ox, oy, oz, hf);
+        const double half = P->step > 0 ? 0.5 * P->dt_prev : 0.0;
+        const double vhx = vx + axp * half, vhy = vy + ayp * half, vhz = vz + azp * half;
+        if (mixed) {
+            r.r5[k] = make_float4(ox, oy, oz, (float)m);
+            r.rv[k] = make_float4((float)vhx, (float)vhy, (float)vhz, 0.5f / hf);
+        } else {
+            f.vhx[k] = vhx;
+            f.vhy[k] = vhy;
+            f.vhz[k] = vhz;
+            f.invh[k] = 1.0 / h;
+        }
+        const int64_t lin = P->cell_base + ((int64_t)cz * P->ncy + cy) * P->ncx + cx;
+        if (k == P->begin || skeys[k - 1] != key) g.cse[lin].x = (uint32_t)k;
+        if (k + 1 == P->end || skeys[k + 1] != key) g.cse[lin].y = (uint32_t)(k + 1);
+        atomicMax((unsigned int*)&g.chmax[lin], __float_as_uint(hf));
+    }
+}
+
+int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint32_t* svals,
+                  const State& src, const State& dst, const uint32_t* perm_src, uint32_t* perm_dst,
+                  const PatchDev* pd, const Grid& g, const Recs& r, const Fp64& f, int mixed)
+{
+    if (n <= 0) return 0;
+    k_gather<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, skeys, svals, src, dst, perm_src,
+                                                                 perm_dst, pd, g, r, f, mixed);
+    return 1;
+}
+
+}  // namespace sphg

@@ -1,0 +1,39 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI and
+put its outputs in the oracle's layout.  Imports nothing from oracle/."""
+import numpy as np
+
+
+def lists_to_original(off, col, perm, n):
+    """CSR in sorted order (rows = sorted particles, cols = sorted indices)
+    -> CSR in original order with ascending columns (the oracle's layout)."""
+    off = np.asarray(off, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    perm = np.asarray(perm, dtype=np.int64)
+    counts = np.diff(off)
+    row_o = np.repeat(perm[:n], counts)
+    col_o = perm[col] if len(col) else col
+    order = np.lexsort((col_o, row_o))
+    off_o = np.zeros(n + 1, dtype=np.int64)
+    off_o[1:] = np.cumsum(np.bincount(row_o, minlength=n))
+    return off_o, col_o[order].astype(np.int32)
+
+
+def normwise(g, o):
+    """max_i |g - o| / max_i |o| (the tolerance norm of reading R16)."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    d = np.abs(o).max()
+    return float(np.abs(g - o).max() / d) if d > 0 else float(np.abs(g - o).max())
+
+
+def scaled(g, o, scale):
+    """max_i |g - o| / scale_i, scale = the sum of the term magnitudes."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    s = np.maximum(np.asarray(scale, dtype=np.float64), 1e-300)
+    return float((np.abs(g - o) / s).max())
+
+
+def zdist(a, b, lz=1.0):
+    d = np.asarray(a) - np.asarray(b)
+    return np.abs(d - lz * np.round(d / lz))

@@ -1,0 +1,191 @@
+"""CUDA path against the FP64 oracle on small seeded inputs (every call goes
+through the C ABI).  Neighbour lists and counts must be bit-exact; the FP64
+path must match within 1e-12 and the mixed path within 1e-5 (relative,
+normwise; du and viscous terms relative to the sum of term magnitudes)."""
+import numpy as np
+import pytest
+
+from paper_1905_03344_gb300 import inputs
+from gpu_common import lists_to_original, normwise, scaled
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1905_03344_gb300 import binding, build
+    build.build()
+    binding.lib()
+    return binding
+
+
+def near_ties(n=600, seed=5, k=3):
+    rng = np.random.default_rng(seed)
+    base = rng.uniform(-0.4, 0.4, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    r = 0.06 * (1.0 + rng.integers(-k, k + 1, n) * 2.0 ** -52)
+    P = np.vstack([base, base + d * r[:, None]])
+    N = 2 * n
+    return {"x": P[:, 0].copy(), "y": P[:, 1].copy(), "z": P[:, 2].copy(),
+            "vx": np.zeros(N), "vy": np.zeros(N), "vz": np.zeros(N),
+            "m": np.full(N, 1.0 / N), "h": np.full(N, 0.03), "u": np.ones(N)}
+
+
+CASES = {
+    "patch20": lambda: inputs.square_patch(20),
+    "cloud": lambda: inputs.random_cloud(3000, seed=1),
+    "hspread": lambda: inputs.random_cloud(2500, seed=2, h_lo=0.01, h_hi=0.15),
+    "irregular": lambda: inputs.irregular_patch(16, seed_pos=3, seed_mass=4),
+    "zwrap": lambda: inputs.random_cloud(900, seed=3, h_lo=0.12, h_hi=0.3),
+    "ties": near_ties,
+}
+
+
+def run_lists(B, f, **kw):
+    n = len(f["x"])
+    sim = B.SPH(max(n, 1), **kw)
+    sim.set_particles(f)
+    sim.find_neighbors()
+    off, col, perm = sim.neighbors()
+    nown = sim.field("nown")
+    nnb = sim.field("nnb")
+    sim.close()
+    o, c = lists_to_original(off, col, perm, n)
+    return o, c, nown, nnb
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_neighbor_lists_bit_exact(B, orc, case):
+    f = CASES[case]()
+    ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+    o, c, nown, nnb = run_lists(B, f)
+    assert np.array_equal(o, ref.off)
+    assert np.array_equal(c, ref.col)
+    assert np.array_equal(nown.astype(np.int64), ref.nown.astype(np.int64))
+    assert np.array_equal(nnb.astype(np.int64), np.diff(ref.off))
+
+
+@pytest.mark.parametrize("tpp", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("cf", [0.5, 0.75, 1.0, 2.5])
+def test_neighbor_lists_any_launch_shape(B, orc, tpp, cf):
+    f = inputs.random_cloud(1500, seed=11, h_lo=0.02, h_hi=0.1)
+    ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+    o, c, nown, _ = run_lists(B, f, threads_per_particle=tpp, cell_factor=cf)
+    assert np.array_equal(o, ref.off) and np.array_equal(c, ref.col)
+    assert np.array_equal(nown.astype(np.int64), ref.nown.astype(np.int64))
+
+
+def _oracle_forces(orc, f):
+    nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+    rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+    P, c = orc.eos(rho, f["u"])
+    ax, ay, az, du, sa, sdu = orc.momentum_energy(f["x"], f["y"], f["z"], f["vx"], f["vy"], f["vz"],
+                                                  f["m"], f["h"], rho, P, c, nb)
+    return dict(rho=rho, P=P, c=c, ax=ax, ay=ay, az=az, du=du, sa=sa, sdu=sdu)
+
+
+def _gpu_forces(B, f, precision, **kw):
+    sim = B.SPH(len(f["x"]), precision=precision, **kw)
+    sim.set_particles(f)
+    sim.find_neighbors()
+    sim.density()
+    sim.momentum_energy()
+    out = {k: sim.field(k) for k in ("rho", "P", "c", "ax", "ay", "az", "du")}
+    sim.close()
+    return out
+
+
+FORCE_CASES = {
+    "patch20": lambda: inputs.square_patch(20),
+    "cloud_av": lambda: inputs.random_cloud(3000, seed=21, vscale=3.0),
+    "irregular": lambda: inputs.irregular_patch(16, seed_pos=6, seed_mass=7),
+    "zwrap": lambda: inputs.random_cloud(900, seed=8, h_lo=0.12, h_hi=0.3, vscale=2.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(FORCE_CASES))
+def test_fp64_pair_sums(B, orc, case):
+    f = FORCE_CASES[case]()
+    o = _oracle_forces(orc, f)
+    g = _gpu_forces(B, f, "fp64")
+    for k in ("rho", "P", "c"):
+        assert normwise(g[k], o[k]) < 1e-12, k
+    for k in ("ax", "ay", "az"):
+        assert normwise(g[k], o[k]) < 1e-12, k
+        assert scaled(g[k], o[k], o["sa"]) < 1e-12, k
+    assert scaled(g["du"], o["du"], o["sdu"]) < 1e-12
+
+
+@pytest.mark.parametrize("case", sorted(FORCE_CASES))
+@pytest.mark.parametrize("tpp", [4, 8, 32])
+def test_mixed_pair_sums(B, orc, case, tpp):
+    f = FORCE_CASES[case]()
+    o = _oracle_forces(orc, f)
+    g = _gpu_forces(B, f, "mixed", threads_per_particle=tpp)
+    for k in ("rho", "P", "c"):
+        assert normwise(g[k], o[k]) < 1e-5, k
+    for k in ("ax", "ay", "az"):
+        assert normwise(g[k], o[k]) < 1e-5, k
+        assert scaled(g[k], o[k], o["sa"]) < 1e-5, k
+    assert scaled(g["du"], o["du"], o["sdu"]) < 1e-5
+
+
+def _compare_state(g, o, tol, what):
+    for k in ("x", "y", "vx", "vy", "vz", "u", "h"):
+        assert normwise(g[k], o[k]) < tol, (what, k, normwise(g[k], o[k]))
+    dz = g["z"] - o["z"]
+    dz -= np.round(dz)
+    assert np.abs(dz).max() < tol * np.abs(o["z"]).max(), (what, "z")
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+def test_square_patch_ten_steps(B, orc, precision, tol):
+    f = inputs.square_patch(20)
+    sim = B.SPH(len(f["x"]), precision=precision)
+    sim.set_particles(f)
+    ref = orc.Sim(f)
+    for step in range(10):
+        dt = sim.step(1)
+        ref.step(1)
+        assert abs(dt - ref.dt) <= tol * ref.dt, (step, dt, ref.dt)
+        g = {k: sim.field(k) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "nown", "rho", "ax")}
+        _compare_state(g, ref, tol, "step %d" % step)
+        assert normwise(g["rho"], ref["rho"]) < tol
+        assert normwise(g["ax"], ref["ax"]) < tol
+    c = sim.conserved()
+    cr = ref.conserved()
+    assert c[0] == pytest.approx(cr[0], rel=1e-14)
+    assert abs(c[4] - cr[4]) < 1e-9 * abs(cr[4])
+    sim.close()
+
+
+def test_batched_patches_match_single(B, orc):
+    rng = np.random.default_rng(3)
+    edges = [6, 9, 7, 11]
+    omegas = rng.uniform(2, 8, len(edges))
+    parts = [inputs.square_patch(e, w) for e, w in zip(edges, omegas)]
+    f = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    offs = np.concatenate([[0], np.cumsum([e ** 3 for e in edges])])
+    sim = B.SPH(len(f["x"]), precision="fp64", max_patches=len(edges))
+    sim.set_particles(f)
+    sim.set_patches(offs)
+    refs = [orc.Sim(p) for p in parts]
+    for step in range(4):
+        sim.step(1)
+        for r in refs:
+            r.step(1)
+        x = sim.field("x")
+        u = sim.field("u")
+        for p, r in enumerate(refs):
+            sl = slice(offs[p], offs[p + 1])
+            assert normwise(x[sl], r["x"]) < 1e-11
+            assert normwise(u[sl], r["u"]) < 1e-11
+            dt, _, nst = sim.dt(p)
+            assert dt == pytest.approx(r.dt, rel=1e-11) and nst == step + 1
+    for p, r in enumerate(refs):
+        c = sim.conserved(p)
+        assert c[0] == pytest.approx(r.conserved()[0], rel=1e-14)
+    sim.close()
