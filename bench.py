@@ -205,12 +205,13 @@ def main():
         return sim
 
     sim = make(args.precision, args.graph)
-    if not args.no_autotune:
-        sim.autotune()
-        sim.set_particles(dfields)
-    tpp, cf = binding.sph_get_tuning(sim.ctx)
     for _ in range(args.warmup):
         sim.step(1)
+    if not args.no_autotune:
+        # tune on the warmed-up state (h adapted); the physical state is unchanged
+        sim.autotune()
+        sim.step(1)
+    tpp, cf = binding.sph_get_tuning(sim.ctx)
     torch.cuda.synchronize()
     sim.pair_count(reset=True)
     if not args.graph:
@@ -290,7 +291,10 @@ def main():
     if args.fp64_steps > 0 and args.precision == "mixed":
         sim.close()
         s64 = make("fp64")
-        s64.step(1)
+        for _ in range(args.warmup):
+            s64.step(1)
+        if not args.no_autotune:
+            s64.autotune()
         torch.cuda.synchronize()
         s64.pair_count(reset=True)
         a0 = torch.cuda.Event(enable_timing=True)
@@ -307,7 +311,10 @@ def main():
         line["mixed_over_fp64"] = line["ms_per_step"] and ms64 / line["ms_per_step"]
         s64.close()
         sim = make(args.precision)
-        sim.autotune() if not args.no_autotune else None
+        for _ in range(args.warmup):
+            sim.step(1)
+        if not args.no_autotune:
+            sim.autotune()
 
     # end to end through the C ABI with host (pinned) buffers
     if args.e2e_steps > 0:

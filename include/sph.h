@@ -196,9 +196,17 @@ sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* c
  * accumulated milliseconds and launch counts per phase (SPH_PHASE_*) and
  * resets them. */
 enum {
-    SPH_PHASE_BBOX = 0, SPH_PHASE_KEYS, SPH_PHASE_SORT, SPH_PHASE_GATHER, SPH_PHASE_NB_COUNT,
-    SPH_PHASE_NB_SCAN, SPH_PHASE_NB_FILL, SPH_PHASE_DENSITY, SPH_PHASE_MOMENTUM,
-    SPH_PHASE_UPDATE, SPH_PHASE_COUNT
+    SPH_PHASE_BBOX = 0,      /* per-patch bounding box, largest h, grid */
+    SPH_PHASE_KEYS,          /* Morton cell keys */
+    SPH_PHASE_SORT,          /* radix sort */
+    SPH_PHASE_GATHER,        /* gather into sorted order, cell table */
+    SPH_PHASE_NB,            /* neighbour lists, single pass with look-back */
+    SPH_PHASE_NB_RESET,      /* look-back state reset */
+    SPH_PHASE_NB_FIXUP,      /* rows longer than their staged slot */
+    SPH_PHASE_DENSITY,       /* density + EOS */
+    SPH_PHASE_MOMENTUM,      /* momentum + energy */
+    SPH_PHASE_UPDATE,        /* dt, kick/drift/AB2, h, conserved sums */
+    SPH_PHASE_COUNT
 };
 sph_status sph_set_profiling(sph_ctx* ctx, int enable);
 sph_status sph_get_profile(sph_ctx* ctx, double* ms, int64_t* launches, int32_t nphase);

@@ -45,7 +45,7 @@ __global__ void k_iota(int64_t n, uint32_t* p)
 
 __global__ void k_accum_pairs(const uint64_t* total, unsigned long long* acc, const int* status)
 {
-    if (!(*status & kStOverflow)) *acc += *total;
+    if (!(*status & kStBad)) *acc += *total;
 }
 
 __global__ void k_fill_patch_of(const WorkItem* items, int nitems, uint16_t* patch_of)
@@ -84,9 +84,11 @@ struct sph_ctx {
     Recs rec{};
     Fp64 f64{};
     uint32_t *cnt = nullptr, *nown = nullptr, *col = nullptr, *col_plain = nullptr;
+    uint32_t *tile_counter = nullptr, *fix_list = nullptr, *fix_count = nullptr;
+    unsigned long long* tile_state = nullptr;
+    int64_t tile_words = 0;
     int64_t col_plain_cap = 0;
-    uint64_t *off = nullptr, *scan64 = nullptr;
-    int64_t scan64_words = 0;
+    uint64_t* off = nullptr;
     PatchDev* pd = nullptr;
     PatchRed* red = nullptr;
     WorkItem* items = nullptr;
@@ -227,10 +229,14 @@ NbArgs nb_args(sph_ctx* ctx)
     a.x = s.x; a.y = s.y; a.z = s.z; a.h = s.h;
     a.cnt = ctx->cnt;
     a.nown = ctx->nown;
-    a.off = ctx->off;
+    a.off_w = ctx->off;
     a.col = ctx->col;
     a.max_pairs = ctx->max_pairs;
     a.status = ctx->status;
+    a.tile_counter = ctx->tile_counter;
+    a.tile_state = ctx->tile_state;
+    a.fix_list = ctx->fix_list;
+    a.fix_count = ctx->fix_count;
     return a;
 }
 
@@ -315,17 +321,19 @@ void enqueue_lists(sph_ctx* ctx)
     const Launch L = launch_of(ctx);
     const NbArgs a = nb_args(ctx);
     {
-        Phase p(ctx, SPH_PHASE_NB_COUNT);
-        ctx->launches += launch_nb_count(L, a, ctx->tpp_nb);
+        Phase p(ctx, SPH_PHASE_NB_RESET);
+        cudaMemsetAsync(ctx->tile_counter, 0, 2 * sizeof(uint32_t), ctx->stream);  // counter + fix count
+        const int64_t ppt_min = 4;
+        const int64_t nt = (ctx->n + ppt_min - 1) / ppt_min + 1;
+        cudaMemsetAsync(ctx->tile_state, 0, sizeof(unsigned long long) * (size_t)nt, ctx->stream);
     }
     {
-        Phase p(ctx, SPH_PHASE_NB_SCAN);
-        ctx->launches += launch_scan_u32_to_u64(L, ctx->n, ctx->cnt, ctx->off, ctx->scan64, ctx->scan64_words);
-        ctx->launches += launch_check_capacity(L, ctx->off + ctx->n, ctx->max_pairs, ctx->status);
+        Phase p(ctx, SPH_PHASE_NB);
+        ctx->launches += launch_nb_lists(L, a, ctx->tpp_nb);
     }
     {
-        Phase p(ctx, SPH_PHASE_NB_FILL);
-        ctx->launches += launch_nb_fill(L, a, ctx->tpp_nb);
+        Phase p(ctx, SPH_PHASE_NB_FIXUP);
+        ctx->launches += launch_nb_fixup(L, a, ctx->tpp_nb);
     }
 }
 
@@ -609,8 +617,12 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     }
     ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->nown, N) && dalloc(ctx, ctx->off, N + 1) &&
          dalloc(ctx, ctx->col, (size_t)ctx->max_pairs);
-    ctx->scan64_words = scan_tmp_words(ctx->cap_n);
-    ok = ok && dalloc(ctx, ctx->scan64, (size_t)ctx->scan64_words);
+    ctx->tile_words = nb_tile_words(ctx->cap_n);
+    uint32_t* tc = nullptr;
+    ok = ok && dalloc(ctx, tc, 2) && dalloc(ctx, ctx->tile_state, (size_t)ctx->tile_words) &&
+         dalloc(ctx, ctx->fix_list, N);
+    ctx->tile_counter = tc;
+    ctx->fix_count = tc ? tc + 1 : nullptr;
     ok = ok && dalloc(ctx, ctx->pd, (size_t)ctx->cap_patch) && dalloc(ctx, ctx->red, (size_t)ctx->cap_patch) &&
          dalloc(ctx, ctx->items, (size_t)ctx->cap_items) && dalloc(ctx, ctx->partials, (size_t)ctx->cap_items * 7) &&
          dalloc(ctx, ctx->cons, (size_t)ctx->cap_patch * 7) && dalloc(ctx, ctx->scratch, N) &&

@@ -30,6 +30,7 @@ constexpr int kStencilCells = 125;             // (2K+1)^3 for K <= 2
 constexpr int kStOverflow = 1;
 constexpr int kStNonFinite = 2;
 constexpr int kStTimeout = 4;
+constexpr int kStBad = kStOverflow | kStNonFinite | kStTimeout;  // later phases skip
 
 // Guard band of the FP32 neighbour pre-filter: a candidate is decided in FP32
 // only when r^2 is outside [T (1 - tol), T (1 + tol)], T the FP64 threshold;
@@ -79,7 +80,7 @@ struct Grid {
 };
 
 struct Recs {             // FP32 records (written by gather / density)
-    float4* r4;          // {ox, oy, oz, h}      neighbour pre-filter
+    float4* r4;          // {ox, oy, oz, 4 h^2}  neighbour pre-filter
     float4* r5;          // {ox, oy, oz, m}      pair sums (mixed)
     float4* rv;          // {vhx, vhy, vhz, 1/(2h)} time-centred velocity (mixed)
     float4* rt;          // {rho, P/rho^2, c, h} thermodynamics (mixed)
@@ -150,9 +151,7 @@ int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint3
                   const State& src, const State& dst, const uint32_t* perm_src,
                   uint32_t* perm_dst, const PatchDev* pd, const Grid& g, const Recs& r,
                   const Fp64& f, int mixed);
-// exclusive scan of n u32 counts into u64 offsets[n+1]; total -> offsets[n]
-int launch_scan_u32_to_u64(const Launch& L, int64_t n, const uint32_t* in, uint64_t* out,
-                           uint64_t* tmp, int64_t tmp_words);
+// temporary words of the device-wide exclusive scan over n values
 int64_t scan_tmp_words(int64_t n);
 
 struct NbArgs {
@@ -163,14 +162,18 @@ struct NbArgs {
     const double *x, *y, *z, *h;
     uint32_t* cnt;
     uint32_t* nown;
-    const uint64_t* off;
+    uint64_t* off_w;
     uint32_t* col;
     int64_t max_pairs;
     int* status;
+    uint32_t* tile_counter;              // next tile of the single-pass build
+    unsigned long long* tile_state;      // look-back words, one per tile
+    uint32_t* fix_list;                  // rows longer than their staged slot
+    uint32_t* fix_count;
 };
-int launch_nb_count(const Launch& L, const NbArgs& a, int tpp);
-int launch_nb_fill(const Launch& L, const NbArgs& a, int tpp);
-int launch_check_capacity(const Launch& L, const uint64_t* total, int64_t max_pairs, int* status);
+int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp);
+int launch_nb_fixup(const Launch& L, const NbArgs& a, int tpp);
+int64_t nb_tile_words(int64_t n);
 int launch_unpack_cols(const Launch& L, int64_t nnz, const uint32_t* col, uint32_t* out);
 
 struct PairArgs {

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 {
     __shared__ float4 tab[kStencilCells];
     fill_stencil_table(tab);
-    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const float gam = (float)a.gamma;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
         const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
         const int zmode = P->zmode;
         const float4 ri = a.r.r5[i];
-        const float hf = a.r.r4[i].w;
+        const float hf = (float)a.s.h[i];
         const float inv2h = 0.5f / hf;
         const uint64_t b = a.off[i], e = a.off[i + 1];
         float sum = 0.0f, comp = 0.0f;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 template <int TPP>
 __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
 {
-    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
 {
     __shared__ float4 tab[kStencilCells];
     fill_stencil_table(tab);
-    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
 template <int TPP>
 __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
 {
-    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const double S80 = 80.0 * kSigmaW;

@@ -311,21 +311,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* in, int64
 
 int64_t scan_tmp_words(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-int launch_scan_u32_to_u64(const Launch& L, int64_t n, const uint32_t* in, uint64_t* out,
-                           uint64_t* tmp, int64_t tmp_words)
-{
-    (void)tmp_words;
-    if (n <= 0) {
-        cudaMemsetAsync(out, 0, sizeof(uint64_t), L.stream);
-        return 0;
-    }
-    const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    k_scan_reduce<uint32_t, uint64_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp);
-    k_scan_spine<uint64_t><<<1, 1024, 0, L.stream>>>(tmp, nb);
-    k_scan_down<uint32_t, uint64_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp, out, 1);
-    return 3;
-}
-
 static int scan_u32(const Launch& L, int64_t n, const uint32_t* in, uint32_t* out, uint32_t* tmp)
 {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
@@ -509,7 +494,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
         const float oy = (float)(y - (P->ymin + (double)cy * P->s));
         const float oz = (float)(z - (-0.5 * P->lz + (double)cz * P->sz));
         const float hf = (float)h;
-        r.r4[k] = make_float4(ox, oy, oz, hf);
+        r.r4[k] = make_float4(ox, oy, oz, 4.0f * hf * hf);
         const double half = P->step > 0 ? 0.5 * P->dt_prev : 0.0;
         const double vhx = vx + axp * half, vhy = vy + ayp * half, vhz = vz + azp * half;
         if (mixed) {

@@ -55,7 +55,7 @@ __device__ __forceinline__ void cons_terms(double x, double y, double vx, double
 __global__ void __launch_bounds__(256) k_hc_min(StepArgs a)
 {
     __shared__ unsigned long long sh[8];
-    if (*a.status & kStOverflow) return;
+    if (*a.status & kStBad) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const WorkItem w = a.items[it];
@@ -91,7 +91,7 @@ int launch_hc_min(const Launch& L, const StepArgs& a)
 __global__ void k_dt(StepArgs a)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.npatch || (*a.status & kStOverflow)) return;
+    if (p >= a.npatch || (*a.status & kStBad)) return;
     PatchDev* P = a.pd + p;
     if (P->end <= P->begin) {
         P->dt = 0.0;
@@ -118,7 +118,7 @@ int launch_dt(const Launch& L, const StepArgs& a)
 __global__ void __launch_bounds__(256) k_update(StepArgs a)
 {
     __shared__ double sh[7][8];
-    if (*a.status & (kStOverflow | kStNonFinite)) return;
+    if (*a.status & kStBad) return;
     for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const WorkItem w = a.items[it];
         const PatchDev* P = a.pd + w.patch;
@@ -210,7 +210,7 @@ __global__ void k_conserved_finalize(StepArgs a, int advance)
     if (t >= a.npatch * 7) return;
     const int p = t / 7, q = t % 7;
     PatchDev* P = a.pd + p;
-    const bool ok = !(*a.status & (kStOverflow | kStNonFinite));
+    const bool ok = !(*a.status & kStBad);
     if (advance && !ok) return;
     double s = 0.0, c = 0.0;
     for (int it = P->item_begin; it < P->item_end; it++) {

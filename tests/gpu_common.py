@@ -26,6 +26,18 @@ def normwise(g, o):
     return float(np.abs(g - o).max() / d) if d > 0 else float(np.abs(g - o).max())
 
 
+def normwise_vec(g3, o3):
+    """Vector field: max over components of max_i |g - o| / max_i |o_i| (Euclidean
+    magnitude).  A component that vanishes by symmetry (a_z, v_z on the
+    z-periodic patch) is rounding noise on both sides; it is measured against
+    the field's magnitude, not against its own noise."""
+    G = np.stack([np.asarray(a, dtype=np.float64) for a in g3])
+    O = np.stack([np.asarray(a, dtype=np.float64) for a in o3])
+    d = np.sqrt((O ** 2).sum(axis=0)).max()
+    e = np.abs(G - O).max()
+    return float(e / d) if d > 0 else float(e)
+
+
 def scaled(g, o, scale):
     """max_i |g - o| / scale_i, scale = the sum of the term magnitudes."""
     g = np.asarray(g, dtype=np.float64)
