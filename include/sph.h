@@ -129,10 +129,13 @@ sph_status sph_set_patches(sph_ctx* ctx, int32_t n_patches, const int64_t* offse
  * Errors: SPH_EOVERFLOW (more than max_pairs entries), SPH_ESTATE. */
 sph_status sph_find_neighbors(sph_ctx* ctx);
 
-/* Borrowed device pointers to the last neighbour lists, in sorted order:
- * row k (sorted particle k) holds col[off[k] .. off[k+1]) as sorted indices;
- * perm[k] is the original index of sorted particle k.  Within a row, columns
- * are grouped by stencil cell.  Any output pointer may be NULL. */
+/* Borrowed device pointers to the last neighbour lists as a canonical CSR in
+ * sorted order: row k (sorted particle k) holds col[off[k] .. off[k+1]) as
+ * sorted indices; perm[k] is the original index of sorted particle k.  Within
+ * a row, columns are grouped by cell, ascending inside each cell.  (The
+ * timestep itself reads the rows where the search wrote them -- contiguous
+ * rows with a start and a length each; this call lays them out with prefix
+ * offsets.)  Any output pointer may be NULL. */
 sph_status sph_get_neighbors(sph_ctx* ctx, const uint64_t** off, const uint32_t** col,
                              const uint32_t** perm, int64_t* nnz);
 
@@ -200,9 +203,8 @@ enum {
     SPH_PHASE_KEYS,          /* Morton cell keys */
     SPH_PHASE_SORT,          /* radix sort */
     SPH_PHASE_GATHER,        /* gather into sorted order, cell table */
-    SPH_PHASE_NB,            /* neighbour lists, single pass with look-back */
-    SPH_PHASE_NB_RESET,      /* look-back state reset */
-    SPH_PHASE_NB_FIXUP,      /* rows longer than their staged slot */
+    SPH_PHASE_NB_RESET,      /* list pool reset */
+    SPH_PHASE_NB,            /* neighbour lists, one warp per 32 particles */
     SPH_PHASE_DENSITY,       /* density + EOS */
     SPH_PHASE_MOMENTUM,      /* momentum + energy */
     SPH_PHASE_UPDATE,        /* dt, kick/drift/AB2, h, conserved sums */

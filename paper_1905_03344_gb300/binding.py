@@ -23,8 +23,7 @@ SPH_KERNEL_WENDLAND = 0
 FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "h", "u", "du_prev", "axp", "ayp", "azp",
           "rho", "P", "c", "ax", "ay", "az", "du", "nown", "nnb"]
 FIELD = {k: i for i, k in enumerate(FIELDS)}
-PHASES = ["bbox", "keys", "sort", "gather", "nb", "nb_reset", "nb_fixup", "density",
-          "momentum", "update"]
+PHASES = ["bbox", "keys", "sort", "gather", "nb_reset", "nb", "density", "momentum", "update"]
 
 
 class SphConfig(ctypes.Structure):

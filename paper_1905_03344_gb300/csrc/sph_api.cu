@@ -43,7 +43,7 @@ __global__ void k_iota(int64_t n, uint32_t* p)
         p[i] = (uint32_t)i;
 }
 
-__global__ void k_accum_pairs(const uint64_t* total, unsigned long long* acc, const int* status)
+__global__ void k_accum_pairs(const unsigned long long* total, unsigned long long* acc, const int* status)
 {
     if (!(*status & kStBad)) *acc += *total;
 }
@@ -70,7 +70,7 @@ struct sph_ctx {
     int cap_patch = 0, cap_items = 0;
     int64_t n = 0;
     int npatch = 0, nitems = 0, radix_passes = 3;
-    int tpp_nb = 4, tpp_pair = 8;
+    int tpp_nb = 1, tpp_pair = 8;
     double cell_factor = 0.5;
     int mixed = 1;
 
@@ -84,9 +84,11 @@ struct sph_ctx {
     Recs rec{};
     Fp64 f64{};
     uint32_t *cnt = nullptr, *nown = nullptr, *col = nullptr, *col_plain = nullptr;
-    uint32_t *tile_counter = nullptr, *fix_list = nullptr, *fix_count = nullptr;
-    unsigned long long* tile_state = nullptr;
-    int64_t tile_words = 0;
+    WorkItem* units = nullptr;     // 32-particle warp units, per patch
+    int64_t nunits = 0, cap_units = 0;
+    unsigned long long *rowstart = nullptr, *pool_used = nullptr;
+    uint64_t* scan64 = nullptr;
+    bool canon_valid = false;      // off / col_plain hold the canonical CSR
     int64_t col_plain_cap = 0;
     uint64_t* off = nullptr;
     PatchDev* pd = nullptr;
@@ -229,14 +231,13 @@ NbArgs nb_args(sph_ctx* ctx)
     a.x = s.x; a.y = s.y; a.z = s.z; a.h = s.h;
     a.cnt = ctx->cnt;
     a.nown = ctx->nown;
-    a.off_w = ctx->off;
+    a.rowstart = ctx->rowstart;
     a.col = ctx->col;
+    a.pool_used = ctx->pool_used;
     a.max_pairs = ctx->max_pairs;
     a.status = ctx->status;
-    a.tile_counter = ctx->tile_counter;
-    a.tile_state = ctx->tile_state;
-    a.fix_list = ctx->fix_list;
-    a.fix_count = ctx->fix_count;
+    a.units = ctx->units;
+    a.nunits = ctx->nunits;
     return a;
 }
 
@@ -246,7 +247,8 @@ PairArgs pair_args(sph_ctx* ctx)
     a.n = ctx->n;
     a.pd = ctx->pd;
     a.patch_of = ctx->patch_of;
-    a.off = ctx->off;
+    a.rowstart = ctx->rowstart;
+    a.cnt = ctx->cnt;
     a.col = ctx->col;
     a.s = ctx->st[ctx->cur];
     a.r = ctx->rec;
@@ -322,18 +324,12 @@ void enqueue_lists(sph_ctx* ctx)
     const NbArgs a = nb_args(ctx);
     {
         Phase p(ctx, SPH_PHASE_NB_RESET);
-        cudaMemsetAsync(ctx->tile_counter, 0, 2 * sizeof(uint32_t), ctx->stream);  // counter + fix count
-        const int64_t ppt_min = 4;
-        const int64_t nt = (ctx->n + ppt_min - 1) / ppt_min + 1;
-        cudaMemsetAsync(ctx->tile_state, 0, sizeof(unsigned long long) * (size_t)nt, ctx->stream);
+        cudaMemsetAsync(ctx->pool_used, 0, sizeof(unsigned long long), ctx->stream);
     }
+    ctx->canon_valid = false;
     {
         Phase p(ctx, SPH_PHASE_NB);
         ctx->launches += launch_nb_lists(L, a, ctx->tpp_nb);
-    }
-    {
-        Phase p(ctx, SPH_PHASE_NB_FIXUP);
-        ctx->launches += launch_nb_fixup(L, a, ctx->tpp_nb);
     }
 }
 
@@ -358,7 +354,7 @@ void enqueue_step(sph_ctx* ctx)
     {
         Phase p(ctx, SPH_PHASE_UPDATE);
         const StepArgs a = step_args(ctx);
-        k_accum_pairs<<<1, 1, 0, ctx->stream>>>(ctx->off + ctx->n, ctx->pair_acc, ctx->status);
+        k_accum_pairs<<<1, 1, 0, ctx->stream>>>(ctx->pool_used, ctx->pair_acc, ctx->status);
         ctx->launches += 1;
         ctx->launches += launch_hc_min(L, a);
         ctx->launches += launch_dt(L, a);
@@ -433,8 +429,23 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
         P.item_end = (int)items.size();
         pd[p] = P;
     }
-    if (cbase > ctx->cap_cells || (int)items.size() > ctx->cap_items)
+    std::vector<WorkItem> units;
+    for (int p = 0; p < np; p++) {
+        for (int64_t b = offsets[p]; b < offsets[p + 1]; b += 32) {
+            WorkItem w;
+            w.begin = b;
+            w.end = b + 32 < offsets[p + 1] ? b + 32 : offsets[p + 1];
+            w.patch = p;
+            w.pad = 0;
+            units.push_back(w);
+        }
+    }
+    if (cbase > ctx->cap_cells || (int)items.size() > ctx->cap_items || (int64_t)units.size() > ctx->cap_units)
         return fail(ctx, SPH_EINVAL, "patch table exceeds capacity");
+    if (!units.empty())
+        CK(cudaMemcpyAsync(ctx->units, units.data(), sizeof(WorkItem) * units.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    ctx->nunits = (int64_t)units.size();
     CK(cudaMemcpyAsync(ctx->pd, pd.data(), sizeof(PatchDev) * np, cudaMemcpyHostToDevice, ctx->stream));
     if (!items.empty())
         CK(cudaMemcpyAsync(ctx->items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
@@ -609,7 +620,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ok = ok && dalloc(ctx, ctx->rec.r4, N);
     if (ctx->mixed) {
         ok = ok && dalloc(ctx, ctx->rec.r5, N) && dalloc(ctx, ctx->rec.rv, N) && dalloc(ctx, ctx->rec.rt, N) &&
-             dalloc(ctx, ctx->rec.hc, N) && dalloc(ctx, ctx->rec.pf, N) && dalloc(ctx, ctx->rec.acc, N);
+             dalloc(ctx, ctx->rec.hc, N) && dalloc(ctx, ctx->rec.pf, N) && dalloc(ctx, ctx->rec.uf, N) &&
+             dalloc(ctx, ctx->rec.acc, N);
     } else {
         Fp64& f = ctx->f64;
         double** g[14] = {&f.vhx, &f.vhy, &f.vhz, &f.rho, &f.P, &f.c, &f.A, &f.hc, &f.invh, &f.ax, &f.ay, &f.az, &f.du, nullptr};
@@ -617,12 +629,10 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     }
     ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->nown, N) && dalloc(ctx, ctx->off, N + 1) &&
          dalloc(ctx, ctx->col, (size_t)ctx->max_pairs);
-    ctx->tile_words = nb_tile_words(ctx->cap_n);
-    uint32_t* tc = nullptr;
-    ok = ok && dalloc(ctx, tc, 2) && dalloc(ctx, ctx->tile_state, (size_t)ctx->tile_words) &&
-         dalloc(ctx, ctx->fix_list, N);
-    ctx->tile_counter = tc;
-    ctx->fix_count = tc ? tc + 1 : nullptr;
+    ctx->cap_units = ctx->cap_n / 32 + ctx->cap_patch + 1;
+    ok = ok && dalloc(ctx, ctx->rowstart, N) && dalloc(ctx, ctx->pool_used, 1) &&
+         dalloc(ctx, ctx->units, (size_t)ctx->cap_units) &&
+         dalloc(ctx, ctx->scan64, (size_t)scan_tmp_words(ctx->cap_n));
     ok = ok && dalloc(ctx, ctx->pd, (size_t)ctx->cap_patch) && dalloc(ctx, ctx->red, (size_t)ctx->cap_patch) &&
          dalloc(ctx, ctx->items, (size_t)ctx->cap_items) && dalloc(ctx, ctx->partials, (size_t)ctx->cap_items * 7) &&
          dalloc(ctx, ctx->cons, (size_t)ctx->cap_patch * 7) && dalloc(ctx, ctx->scratch, N) &&
@@ -703,8 +713,8 @@ sph_status sph_find_neighbors(sph_ctx* ctx)
     enqueue_lists(ctx);
     st = after_launches(ctx, "sph_find_neighbors");
     if (st != SPH_OK) return st;
-    uint64_t nnz = 0;
-    CK(cudaMemcpyAsync(&nnz, ctx->off + ctx->n, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long nnz = 0;
+    CK(cudaMemcpyAsync(&nnz, ctx->pool_used, sizeof(nnz), cudaMemcpyDeviceToHost, ctx->stream));
     st = check_status(ctx, "sph_find_neighbors");
     ctx->nnz = (int64_t)nnz;
     if (st != SPH_OK) return st;
@@ -718,7 +728,9 @@ sph_status sph_get_neighbors(sph_ctx* ctx, const uint64_t** off, const uint32_t*
     sph_status st = begin_call(ctx);
     if (st != SPH_OK) return st;
     if (!ctx->nb_valid) return fail(ctx, SPH_ESTATE, "no current neighbour lists");
-    if (col) {
+    if (!ctx->canon_valid) {
+        // canonical CSR from the list pool: prefix offsets of the row lengths,
+        // rows copied in particle order
         if (ctx->col_plain_cap < ctx->nnz) {
             if (ctx->col_plain) {
                 for (auto& q : ctx->allocs)
@@ -733,10 +745,13 @@ sph_status sph_get_neighbors(sph_ctx* ctx, const uint64_t** off, const uint32_t*
             ctx->col_plain = p;
             ctx->col_plain_cap = ctx->nnz;
         }
-        ctx->launches += launch_unpack_cols(launch_of(ctx), ctx->nnz, ctx->col, ctx->col_plain);
+        ctx->launches += launch_scan_u32_to_u64(launch_of(ctx), ctx->n, ctx->cnt, ctx->off, ctx->scan64);
+        ctx->launches += launch_canonical_rows(launch_of(ctx), ctx->n, ctx->rowstart, ctx->cnt, ctx->off,
+                                               ctx->col, ctx->col_plain);
         CK(cudaStreamSynchronize(ctx->stream));
-        *col = ctx->col_plain;
+        ctx->canon_valid = true;
     }
+    if (col) *col = ctx->col_plain;
     if (off) *off = ctx->off;
     if (perm) *perm = ctx->perm[ctx->cur];
     if (nnz) *nnz = ctx->nnz;
@@ -907,7 +922,7 @@ sph_status sph_get_field(sph_ctx* ctx, int32_t field, double* dst, int on_device
         ctx->launches += launch_unpermute_u32(L, n, ctx->nown, perm, out);
     } else {
         if (ctx->fresh) return fail(ctx, SPH_ESTATE, "no neighbour search yet");
-        ctx->launches += launch_row_lengths(L, n, ctx->off, perm, out);
+        ctx->launches += launch_unpermute_u32(L, n, ctx->cnt, perm, out);
     }
     st = after_launches(ctx, "sph_get_field");
     if (st != SPH_OK) return st;
@@ -1036,7 +1051,8 @@ sph_status sph_autotune(sph_ctx* ctx)
     ctx->prof = false;
     destroy_graphs(ctx);
     const double factors[3] = {0.5, 0.75, 1.0};
-    const int tpps[4] = {2, 4, 8, 16};
+    const int nb_tpps[2] = {1, 32};
+    const int pair_tpps[4] = {4, 8, 16, 32};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1059,15 +1075,15 @@ sph_status sph_autotune(sph_ctx* ctx)
         ctx->cell_factor = f;
         enqueue_sort(ctx);
         float bnb = 1e30f, bpair = 1e30f;
-        int tnb = 4, tpair = 8;
-        for (int t : tpps) {
+        int tnb = 1, tpair = 8;
+        for (int t : nb_tpps) {
             ctx->tpp_nb = t;
             float ms = timeit([&] { enqueue_lists(ctx); });
             if (ms < bnb) { bnb = ms; tnb = t; }
         }
         ctx->tpp_nb = tnb;
         enqueue_lists(ctx);
-        for (int t : tpps) {
+        for (int t : pair_tpps) {
             ctx->tpp_pair = t;
             float ms = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
             if (ms < bpair) { bpair = ms; tpair = t; }

@@ -34,11 +34,12 @@ constexpr int kStBad = kStOverflow | kStNonFinite | kStTimeout;  // later phases
 
 // Guard band of the FP32 neighbour pre-filter: a candidate is decided in FP32
 // only when r^2 is outside [T (1 - tol), T (1 + tol)], T the FP64 threshold;
-// otherwise the exact FP64 predicate decides.  tol = 2^-13 + 2^-19 s/h_i
-// bounds the FP32 rounding of the cell-relative r^2 (error ~ 12 * 2^-24 s/h
-// relative to T) with a margin of more than 2x.
+// otherwise the exact FP64 predicate decides.  tol = 2^-13 + 2^-16 s/h_i
+// bounds the FP32 rounding of r^2 computed from cell-relative coordinates
+// shifted by at most 3 cells (error below 60 * 2^-24 s/h relative to T) with
+// a margin of more than 4x.
 constexpr float kTolBase = 1.0f / 8192.0f;
-constexpr float kTolCell = 1.0f / 524288.0f;
+constexpr float kTolCell = 1.0f / 65536.0f;
 // Cell edges carry a relative margin so that FP32 cell assignment can never
 // separate two particles closer than 2 h_max by more than K cells.
 constexpr double kCellMargin = 1.0 + 1.0 / 1024.0;
@@ -86,6 +87,7 @@ struct Recs {             // FP32 records (written by gather / density)
     float4* rt;          // {rho, P/rho^2, c, h} thermodynamics (mixed)
     float* hc;           // h/c (mixed)
     float* pf;           // P (mixed)
+    float* uf;           // u, staged by the gather (mixed)
     float4* acc;         // {ax, ay, az, du} (mixed)
 };
 
@@ -160,27 +162,28 @@ struct NbArgs {
     Grid g;
     const float4* r4;
     const double *x, *y, *z, *h;
-    uint32_t* cnt;
-    uint32_t* nown;
-    uint64_t* off_w;
-    uint32_t* col;
+    const WorkItem* units;               // 32 consecutive particles of one patch each
+    int64_t nunits;
+    uint32_t* cnt;                       // |N(i)|
+    uint32_t* nown;                      // n_i
+    unsigned long long* rowstart;        // first pool entry of row i
+    uint32_t* col;                       // the list pool
+    unsigned long long* pool_used;       // entries reserved so far
     int64_t max_pairs;
     int* status;
-    uint32_t* tile_counter;              // next tile of the single-pass build
-    unsigned long long* tile_state;      // look-back words, one per tile
-    uint32_t* fix_list;                  // rows longer than their staged slot
-    uint32_t* fix_count;
 };
 int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp);
-int launch_nb_fixup(const Launch& L, const NbArgs& a, int tpp);
-int64_t nb_tile_words(int64_t n);
-int launch_unpack_cols(const Launch& L, int64_t nnz, const uint32_t* col, uint32_t* out);
+int launch_canonical_rows(const Launch& L, int64_t n, const unsigned long long* rowstart,
+                          const uint32_t* cnt, const uint64_t* off, const uint32_t* col, uint32_t* out);
+// exclusive scan of n u32 values into u64 out[0..n], out[n] = total
+int launch_scan_u32_to_u64(const Launch& L, int64_t n, const uint32_t* in, uint64_t* out, uint64_t* tmp);
 
 struct PairArgs {
     int64_t n;
     const PatchDev* pd;
     const uint16_t* patch_of;
-    const uint64_t* off;
+    const unsigned long long* rowstart;  // row i is col[rowstart[i] .. + cnt[i])
+    const uint32_t* cnt;
     const uint32_t* col;
     State s;
     Recs r;
@@ -220,8 +223,6 @@ int launch_unpermute_f32(const Launch& L, int64_t n, const float* src, int strid
                          const uint32_t* perm, double* dst);
 int launch_unpermute_u32(const Launch& L, int64_t n, const uint32_t* src, const uint32_t* perm,
                          double* dst);
-int launch_row_lengths(const Launch& L, int64_t n, const uint64_t* off, const uint32_t* perm,
-                       double* dst);
 int launch_validate(const Launch& L, int64_t n, const State& s, int* status);
 int launch_reset_red(const Launch& L, int npatch, PatchRed* red);
 

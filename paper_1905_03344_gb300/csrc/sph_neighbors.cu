@@ -1,38 +1,56 @@
 // sph_neighbors.cu -- neighbour discovery, second half: symmetric neighbour
-// lists in CSR form (Table 1 "Neighbour Discovery", symmetric union reading
-// R11): j is in N(i) iff j != i and r_ij^2 < 4 h_i^2 or r_ij^2 < 4 h_j^2,
-// with the minimum image along periodic z.  n_i = #{j : r_ij^2 < 4 h_i^2}
-// feeds the smoothing-length adaptation.
+// lists (Table 1 "Neighbour Discovery", symmetric union reading R11): j is
+// in N(i) iff j != i and r_ij^2 < 4 h_i^2 or r_ij^2 < 4 h_j^2, with the
+// minimum image along periodic z.  n_i = #{j : r_ij^2 < 4 h_i^2} feeds the
+// smoothing-length adaptation.
 //
-// Each particle is served by a group of TPP lanes.  The group walks the
-// (2K+1)^3 cells around the particle's cell, skipping cells whose box is
-// farther than 2 max(h_i, h_max(cell)), and tests candidates in FP32 on
-// cell-relative coordinates.  A candidate is decided in FP32 only outside a
-// guard band around the threshold; inside it the FP64 predicate is evaluated
-// with the same operation order and rounding as its definition, so the lists
-// are bit-exact.
+// One warp serves 32 consecutive sorted particles of one patch, one lane per
+// particle.  The warp expresses its particles in the frame of a reference
+// cell, takes their bounding box, and enumerates the block of cells around
+// it, keeping the non-empty cells closer than 2 max(h_warp, h_max(cell)).
+// The candidates of the kept cells are staged 32 at a time in shared memory
+// (shifted into the reference frame) and every lane tests all 32 against its
+// own particle, so each candidate is loaded once per warp and the inner loop
+// is a shared-memory broadcast plus FP32 arithmetic.  A candidate is decided
+// in FP32 only outside a guard band around the threshold; inside it the FP64
+// predicate is evaluated with the same operation order and rounding as its
+// definition, so the lists are bit-exact.  Lanes farther than kSpanMax cells
+// from the reference cell are served in a later pass of the same warp.
 //
-// One pass builds the CSR: a CTA takes the next tile of consecutive sorted
-// particles (tile ids handed out in launch order by an atomic counter),
-// stages each particle's row in shared memory (ordered by stencil cell, then
-// by sorted index, through a ballot inside the group), scans the row lengths
-// of the tile, and obtains the tile's global offset by a decoupled look-back
-// over the preceding tiles' published sums.  The rows are then written with
-// coalesced stores.  Rows longer than their shared-memory slot are recorded
-// and written in full by a fix-up pass that repeats their search.  The
-// look-back only waits for tiles handed out earlier (already running), and
-// every wait is bounded: past the limit the kernel reports SPH_ETIMEOUT
-// through the status word instead of spinning on.
+// Each lane stages its row in shared memory (ordered by position in the cell
+// block, then by sorted index); the warp then reserves the rows of the pass
+// in the list pool with one atomic add and writes them with coalesced
+// stores.  Rows longer than the staging slot are written straight to the
+// pool by a second walk over the same candidates.  Row contents are fixed by
+// the inputs; only the place of a warp's rows in the pool depends on
+// scheduling, and every consumer reads a row through its start and length,
+// so all results are bitwise reproducible.  The canonical CSR with prefix
+// offsets is built from the pool on demand (sph_get_neighbors).  Nothing
+// waits on another warp.
 #include "sph_internal.cuh"
 
 namespace sphg {
 
-constexpr int kNbThreads = 128;
-constexpr int kNbSmemWords = 8192;                // 32 KB of staged rows per CTA
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
-constexpr long long kSpinLimit = 1ll << 24;
+constexpr int kNbWarps = 2;            // warps per CTA
+constexpr int kRowCap = 128;           // staged entries per lane
+constexpr int kRowStride = kRowCap + 1;
+constexpr int kKeptMax = 64;           // kept-cell batch
+constexpr int kSpanMax = 2;            // cells between a lane and the reference cell
+
+struct NbWarpSmem {
+    uint32_t rows[32 * kRowStride];    // staged rows, one per lane
+    float4 tq[32];                     // candidate tile: position in the reference frame, 4 h^2
+    uint32_t tj[32];                   // candidate index
+    uint32_t tb[32];                   // candidate cell, packed offset from the reference cell
+    uint32_t kst[kKeptMax];            // kept cells: first particle
+    uint32_t kpre[kKeptMax];           // kept cells: prefix of the lengths
+    uint32_t kb[kKeptMax];             // kept cells: packed offset from the reference cell
+};
+
+__device__ __forceinline__ uint32_t pack3(int bx, int by, int bz)
+{
+    return (uint32_t)(bx + 128) | ((uint32_t)(by + 128) << 8) | ((uint32_t)(bz + 128) << 16);
+}
 
 // exact FP64 predicate, no contraction: bit 0 union, bit 1 own radius
 __device__ __forceinline__ int exact_pair(double xi, double yi, double zi, double hi, double xj,
@@ -50,30 +68,315 @@ __device__ __forceinline__ int exact_pair(double xi, double yi, double zi, doubl
     return (own | oth) | (own << 1);
 }
 
-// distance from a point at cell-relative coordinate o in [0, s) to the cell
-// offset by d cells along one axis
-__device__ __forceinline__ float cell_gap(int d, float o, float s)
+__device__ __forceinline__ float warp_min(float v)
 {
-    float g = d > 0 ? (float)d * s - o : (d < 0 ? o - (float)(d + 1) * s : 0.0f);
-    return fmaxf(g, 0.0f);
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-// The search for particle i by a group of TPP lanes.  emit(pos, word) is
-// called by each lane holding a neighbour, pos being its index in the row;
-// returns the row length (uniform in the group) and adds to own.
-template <int TPP, class Emit>
-__device__ __forceinline__ uint32_t search_row(const NbArgs& a, int64_t i, int gl, unsigned gmask,
-                                               unsigned ltmask, uint32_t& own, Emit emit)
+// gap between [lo, hi] and the cell [b s, (b+1) s) along one axis
+__device__ __forceinline__ float box_gap(float lo, float hi, int b, float s)
 {
-    const PatchDev* P = a.pd + a.g.patch_of[i];
-    const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
+    const float c0 = (float)b * s, c1 = c0 + s;
+    return fmaxf(fmaxf(c0 - hi, lo - c1), 0.0f);
+}
+
+struct LaneState {
+    float ox, oy, oz;      // particle in the reference frame
+    float Ti, flo, fhi;    // 4 h_i^2 and the guard band
+    int dx, dy, dz;        // cell offset from the reference cell
+    uint32_t kki;          // (dx + 5 dy + 25 dz) << kColBits
+    uint32_t cnt, own;
+    int64_t i;
+    bool act;              // lane takes part in this pass
+};
+
+struct WarpBox {
+    int refx, refy, refz;
+    float x0, y0, z0, x1, y1, z1;  // bounding box of the pass, reference frame
+    float hw;                      // largest h of the pass
+};
+
+// One walk over the candidates of the lanes in L.act.  DIRECT = false: rows
+// are staged in shared memory (up to kRowCap entries); DIRECT = true: lanes
+// with direct = true write their whole row to the pool at r0.
+template <bool DIRECT>
+__device__ void warp_walk(const NbArgs& a, const PatchDev* P, NbWarpSmem& S, LaneState& L, int lane,
+                          const WarpBox& B, bool direct, unsigned long long r0)
+{
+    const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
+    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz, zmode = P->zmode;
+    const uint32_t cbase = (uint32_t)P->cell_base;
+    const float slack = (1.0f / 4096.0f) * s_f;
+    const float Rmax = 2.0f * fmaxf(B.hw, P->hmax_f) * (1.0f + 1.0f / 512.0f) + slack;
+    // block of cells around the bounding box, as offsets from the reference cell
+    const int xlo = max((int)floorf((B.x0 - Rmax) / s_f), -B.refx);
+    const int xhi = min((int)floorf((B.x1 + Rmax) / s_f), ncx - 1 - B.refx);
+    const int ylo = max((int)floorf((B.y0 - Rmax) / s_f), -B.refy);
+    const int yhi = min((int)floorf((B.y1 + Rmax) / s_f), ncy - 1 - B.refy);
+    const int zlo = (int)floorf((B.z0 - Rmax) / sz_f);
+    int zhi = (int)floorf((B.z1 + Rmax) / sz_f);
+    // a block longer than the period would visit a z cell twice: take one
+    // full period instead and the minimum image in FP32
+    const bool zwrap = zmode != 0 || (zhi - zlo + 1) >= ncz;
+    if (zwrap) zhi = zlo + ncz - 1;
+    const int nbx = xhi - xlo + 1, nby = yhi - ylo + 1, nbz = zhi - zlo + 1;
+    const int nbox = (nbx > 0 && nby > 0) ? nbx * nby * nbz : 0;
+    const unsigned ltmask = (1u << lane) - 1u;
+    uint32_t nk = 0, ktot = 0;
+
+    auto flush = [&]() {
+        // candidates of the kept batch, 32 per tile
+        for (uint32_t fb = 0; fb < ktot; fb += 32) {
+            const uint32_t f = fb + lane;
+            if (f < ktot) {
+                uint32_t c = 0;
+                while (c + 1 < nk && S.kpre[c + 1] <= f) c++;
+                const uint32_t j = S.kst[c] + (f - S.kpre[c]);
+                const uint32_t pb = S.kb[c];
+                const float4 q = a.r4[j];
+                const int bx = (int)(pb & 255u) - 128, by = (int)((pb >> 8) & 255u) - 128,
+                          bz = (int)((pb >> 16) & 255u) - 128;
+                S.tq[lane] = make_float4(fmaf((float)bx, s_f, q.x), fmaf((float)by, s_f, q.y),
+                                         fmaf((float)bz, sz_f, q.z), q.w);
+                // column word for a particle of the reference cell; a lane d cells
+                // away subtracts d from the stencil code (exact when |offset| <= 2)
+                S.tj[lane] = j | ((uint32_t)((bx + 2) + 5 * (by + 2) + 25 * (bz + 2)) << kColBits);
+                S.tb[lane] = pb;
+            }
+            __syncwarp();
+            const uint32_t nt = min(32u, ktot - fb);
+            if (L.act) {
+                for (uint32_t t = 0; t < nt; t++) {
+                    const float4 Q = S.tq[t];
+                    const float ex = L.ox - Q.x, ey = L.oy - Q.y;
+                    float ez = L.oz - Q.z;
+                    // the block may start a whole period away: nearest image
+                    if (zwrap) ez = fmaf(-lz_f, rintf(ez * inv_lz), ez);
+                    const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const float T = fmaxf(L.Ti, Q.w);
+                    if (r2 > T * L.fhi) continue;
+                    const uint32_t tw = S.tj[t];
+                    const uint32_t j = tw & kColMask;
+                    if ((int64_t)j == L.i) continue;
+                    bool in = r2 < T * L.flo;
+                    bool io = r2 < L.Ti * L.flo;
+                    if (!in || (!io && r2 <= L.Ti * L.fhi)) {
+                        const int e = exact_pair(a.x[L.i], a.y[L.i], a.z[L.i], a.h[L.i], a.x[j], a.y[j], a.z[j],
+                                                 a.h[j], P->lz);
+                        in = e & 1;
+                        io = (e >> 1) & 1;
+                    }
+                    L.own += io;
+                    if (!in) continue;
+                    uint32_t w;
+                    if (!zwrap) {
+                        w = tw - L.kki;
+                    } else {
+                        // stencil code of j's cell relative to i's cell, periodic z
+                        const uint32_t pb = S.tb[t];
+                        const int dcx = (int)(pb & 255u) - 128 - L.dx;
+                        const int dcy = (int)((pb >> 8) & 255u) - 128 - L.dy;
+                        int dcz = (int)((pb >> 16) & 255u) - 128 - L.dz;
+                        int zd;
+                        if (zmode == 0) {
+                            dcz = ((dcz % ncz) + ncz) % ncz;
+                            if (dcz > ncz / 2) dcz -= ncz;
+                            zd = dcz + 2;
+                        } else {
+                            zd = ((dcz % ncz) + ncz) % ncz;
+                        }
+                        w = j | ((uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd) << kColBits);
+                    }
+                    if (DIRECT) {
+                        if (direct && r0 + L.cnt < (unsigned long long)a.max_pairs) a.col[r0 + L.cnt] = w;
+                    } else if (L.cnt < (uint32_t)kRowCap) {
+                        S.rows[lane * kRowStride + L.cnt] = w;
+                    }
+                    L.cnt++;
+                }
+            }
+            __syncwarp();
+        }
+        nk = 0;
+        ktot = 0;
+    };
+
+    for (int cb = 0; cb < nbox; cb += 32) {
+        const int c = cb + lane;
+        bool keep = false;
+        uint32_t st = 0, len = 0, pb = 0;
+        if (c < nbox) {
+            const int bx = xlo + c % nbx, by = ylo + (c / nbx) % nby, bz = zlo + c / (nbx * nby);
+            const int cxj = B.refx + bx, cyj = B.refy + by;
+            int czj = (B.refz + bz) % ncz;
+            if (czj < 0) czj += ncz;
+            const float gz = zwrap ? 0.0f : box_gap(B.z0, B.z1, bz, sz_f);
+            const float gx = box_gap(B.x0, B.x1, bx, s_f), gy = box_gap(B.y0, B.y1, by, s_f);
+            const float d2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+            if (d2 < Rmax * Rmax) {
+                const uint32_t lin =
+                    cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cxj;
+                const uint2 se = a.g.cse[lin];
+                if (se.x < se.y) {
+                    const float R = 2.0f * fmaxf(B.hw, a.g.chmax[lin]) * (1.0f + 1.0f / 512.0f) + slack;
+                    if (d2 < R * R) {
+                        keep = true;
+                        st = se.x;
+                        len = se.y - se.x;
+                        pb = pack3(bx, by, bz);
+                    }
+                }
+            }
+        }
+        uint32_t inc = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const uint32_t k = nk + (uint32_t)__popc(b & ltmask);
+            S.kst[k] = st;
+            S.kpre[k] = ktot + inc - len;
+            S.kb[k] = pb;
+        }
+        nk += (uint32_t)__popc(b);
+        ktot += __shfl_sync(0xffffffffu, inc, 31);
+        __syncwarp();
+        if (nk > (uint32_t)(kKeptMax - 32) || cb + 32 >= nbox) flush();
+    }
+}
+
+__global__ void __launch_bounds__(32 * kNbWarps) k_nb_warp(NbArgs a)
+{
+    extern __shared__ __align__(16) unsigned char nb_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    NbWarpSmem& S = ((NbWarpSmem*)nb_smem)[warp];
+    if (*a.status & kStBad) return;
+    for (int64_t q = (int64_t)blockIdx.x * kNbWarps + warp; q < a.nunits; q += (int64_t)gridDim.x * kNbWarps) {
+        const WorkItem U = a.units[q];
+        const PatchDev* P = a.pd + U.patch;
+        const float s_f = P->s_f, sz_f = P->sz_f;
+        const int ncz = P->ncz;
+        const int64_t i = U.begin + lane;
+        const bool valid = i < U.end;
+        LaneState L;
+        L.i = i;
+        float4 r = make_float4(0.f, 0.f, 0.f, 1.f);
+        uint32_t cc = 0;
+        float hf = 1.0f;
+        if (valid) {
+            r = a.r4[i];
+            cc = a.g.cellxyz[i];
+            hf = (float)a.h[i];
+        }
+        const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
+        const float tol = kTolBase + kTolCell * (s_f / hf);
+        L.Ti = r.w;
+        L.flo = 1.0f - tol;
+        L.fhi = 1.0f + tol;
+        unsigned pending = __ballot_sync(0xffffffffu, valid);
+        while (pending) {
+            // reference cell: the first pending lane; the lanes within kSpanMax
+            // cells of it form this pass
+            const int ref = __ffs(pending) - 1;
+            WarpBox B;
+            B.refx = __shfl_sync(0xffffffffu, cx, ref);
+            B.refy = __shfl_sync(0xffffffffu, cy, ref);
+            B.refz = __shfl_sync(0xffffffffu, cz, ref);
+            L.dx = cx - B.refx;
+            L.dy = cy - B.refy;
+            int dz = cz - B.refz;
+            if (dz > ncz / 2) dz -= ncz;
+            else if (dz < -(ncz / 2)) dz += ncz;
+            L.dz = dz;
+            L.kki = (uint32_t)(L.dx + 5 * L.dy + 25 * L.dz) << kColBits;
+            L.act = ((pending >> lane) & 1u) && abs(L.dx) <= kSpanMax && abs(L.dy) <= kSpanMax &&
+                    abs(L.dz) <= kSpanMax;
+            const unsigned actm = __ballot_sync(0xffffffffu, L.act);
+            L.ox = fmaf((float)L.dx, s_f, r.x);
+            L.oy = fmaf((float)L.dy, s_f, r.y);
+            L.oz = fmaf((float)L.dz, sz_f, r.z);
+            B.x0 = warp_min(L.act ? L.ox : 3.4e38f);
+            B.x1 = warp_max(L.act ? L.ox : -3.4e38f);
+            B.y0 = warp_min(L.act ? L.oy : 3.4e38f);
+            B.y1 = warp_max(L.act ? L.oy : -3.4e38f);
+            B.z0 = warp_min(L.act ? L.oz : 3.4e38f);
+            B.z1 = warp_max(L.act ? L.oz : -3.4e38f);
+            B.hw = warp_max(L.act ? hf : 0.0f);
+            L.cnt = 0;
+            L.own = 0;
+            warp_walk<false>(a, P, S, L, lane, B, false, 0);
+            // reserve the rows of this pass in the pool and write them out
+            const uint32_t v = L.act ? L.cnt : 0u;
+            uint32_t inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+            unsigned long long base = 0;
+            if (lane == 0) {
+                base = atomicAdd(a.pool_used, (unsigned long long)tot);
+                if (base + tot > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
+            }
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const unsigned long long r0 = base + (inc - v);
+            const bool fits = base + tot <= (unsigned long long)a.max_pairs;
+            if (L.act) {
+                a.rowstart[i] = r0;
+                a.cnt[i] = L.cnt;
+                a.nown[i] = L.own;
+            }
+            if (fits) {
+                for (int l = 0; l < 32; l++) {
+                    if (!((actm >> l) & 1u)) continue;
+                    const uint32_t len = min(__shfl_sync(0xffffffffu, L.cnt, l), (uint32_t)kRowCap);
+                    const unsigned long long rs = __shfl_sync(0xffffffffu, r0, l);
+                    for (uint32_t k = lane; k < len; k += 32) a.col[rs + k] = S.rows[l * kRowStride + k];
+                }
+                const bool direct = L.act && L.cnt > (uint32_t)kRowCap;
+                if (__ballot_sync(0xffffffffu, direct)) {
+                    // rows longer than the staging slot: same walk, written to the pool
+                    const uint32_t keep_cnt = L.cnt, keep_own = L.own;
+                    L.cnt = 0;
+                    L.own = 0;
+                    warp_walk<true>(a, P, S, L, lane, B, direct, r0);
+                    L.cnt = keep_cnt;
+                    L.own = keep_own;
+                }
+            }
+            __syncwarp();
+            pending &= ~actm;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Thread-per-particle variant: each lane walks the (2K+1)^3 cells around its
+// own cell with its own pruning, in the same loop order as the other lanes of
+// its warp (lanes of one cell load the same candidates at the same time), and
+// stages its row in shared memory like the warp-tile kernel.
+// DIRECT: lanes with direct = true write their whole row to the pool at r0.
+// ---------------------------------------------------------------------------
+template <bool DIRECT>
+__device__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t* row, bool direct,
+                                unsigned long long r0, uint32_t& own)
+{
+    const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
     const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz, K = P->K, zmode = P->zmode;
-    const int64_t cbase = P->cell_base;
+    const uint32_t cbase = (uint32_t)P->cell_base;
     const float4 ri = a.r4[i];
     const uint32_t cc = a.g.cellxyz[i];
     const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
     const float hf = (float)a.h[i];
-    const float Ti = ri.w;                                  // 4 h_i^2
+    const float Ti = ri.w;
     const float tol = kTolBase + kTolCell * (s_f / hf);
     const float flo = 1.0f - tol, fhi = 1.0f + tol;
     const float slack = (1.0f / 4096.0f) * s_f;
@@ -90,7 +393,8 @@ __device__ __forceinline__ uint32_t search_row(const NbArgs& a, int64_t i, int g
             if (czj < 0) czj += ncz;
             else if (czj >= ncz) czj -= ncz;
             zsh = (float)dcz * sz_f;
-            gz = cell_gap(dcz, ri.z, sz_f);
+            const float g = dcz > 0 ? (float)dcz * sz_f - ri.z : (dcz < 0 ? ri.z - (float)(dcz + 1) * sz_f : 0.0f);
+            gz = fmaxf(g, 0.0f);
             zd = dcz + 2;
         } else {
             czj = cz + iz;
@@ -105,50 +409,66 @@ __device__ __forceinline__ uint32_t search_row(const NbArgs& a, int64_t i, int g
         for (int dcy = -K; dcy <= K; dcy++) {
             const int cyj = cy + dcy;
             if (cyj < 0 || cyj >= ncy) continue;
-            const float gy = cell_gap(dcy, ri.y, s_f);
+            const float g = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : 0.0f);
+            const float gy = fmaxf(g, 0.0f);
             const float gzy2 = fmaf(gy, gy, gz2);
             if (gzy2 >= Rg2) continue;
             const float yo = ri.y - (float)dcy * s_f;
             for (int dcx = -K; dcx <= K; dcx++) {
                 const int cxj = cx + dcx;
                 if (cxj < 0 || cxj >= ncx) continue;
-                const float gx = cell_gap(dcx, ri.x, s_f);
+                const float gg = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : 0.0f);
+                const float gx = fmaxf(gg, 0.0f);
                 const float d2 = fmaf(gx, gx, gzy2);
-                const int64_t lin = cbase + ((int64_t)czj * ncy + cyj) * ncx + cxj;
+                if (d2 >= Rg2) continue;
+                const uint32_t lin =
+                    cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cxj;
                 const uint2 se = a.g.cse[lin];
+                const float hc = a.g.chmax[lin];
                 if (se.x >= se.y) continue;
-                const float R = 2.0f * fmaxf(hf, a.g.chmax[lin]) * (1.0f + 1.0f / 512.0f) + slack;
+                const float R = 2.0f * fmaxf(hf, hc) * (1.0f + 1.0f / 512.0f) + slack;
                 if (d2 >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
                 const uint32_t kk = (uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd) << kColBits;
-                for (uint32_t jb = se.x; jb < se.y; jb += TPP) {
-                    const uint32_t j = jb + gl;
-                    bool in = false;
-                    if (j < se.y) {
-                        const float4 q = a.r4[j];
-                        const float dx = xo - q.x, dy = yo - q.y;
-                        float dz = zo - q.z;
-                        if (zmode) {
-                            if (dz > 0.5f * lz_f) dz -= lz_f;
-                            else if (dz < -0.5f * lz_f) dz += lz_f;
-                        }
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float T = fmaxf(Ti, q.w);
-                        if (r2 <= T * fhi && (int64_t)j != i) {
-                            in = r2 < T * flo;
-                            bool io = r2 < Ti * flo;
-                            if (!in || (!io && r2 <= Ti * fhi)) {
-                                const int e = exact_pair(a.x[i], a.y[i], a.z[i], a.h[i], a.x[j], a.y[j],
-                                                         a.z[j], a.h[j], P->lz);
-                                in = e & 1;
-                                io = (e >> 1) & 1;
-                            }
-                            own += io;
-                        }
+                // four candidates per iteration: the gathers are in flight together
+                for (uint32_t jb = se.x; jb < se.y; jb += 4) {
+                    float4 q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) q[u] = a.r4[min(jb + (uint32_t)u, se.y - 1u)];
+                    float r2[4], T[4];
+                    unsigned near = 0;
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const float dx = xo - q[u].x, dy = yo - q[u].y;
+                        float dz = zo - q[u].z;
+                        if (zmode) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
+                        r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        T[u] = fmaxf(Ti, q[u].w);
+                        const uint32_t j = jb + (uint32_t)u;
+                        if (j < se.y && r2[u] <= T[u] * fhi && (int64_t)j != i) near |= 1u << u;
                     }
-                    const unsigned b = __ballot_sync(gmask, in);
-                    if (in) emit(cnt + (uint32_t)__popc(b & ltmask), j | kk);
-                    cnt += (uint32_t)__popc(b);
+                    if (!near) continue;
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        if (!(near & (1u << u))) continue;
+                        const uint32_t j = jb + (uint32_t)u;
+                        bool in = r2[u] < T[u] * flo;
+                        bool io = r2[u] < Ti * flo;
+                        if (!in || (!io && r2[u] <= Ti * fhi)) {
+                            const int e = exact_pair(a.x[i], a.y[i], a.z[i], a.h[i], a.x[j], a.y[j], a.z[j],
+                                                     a.h[j], P->lz);
+                            in = e & 1;
+                            io = (e >> 1) & 1;
+                        }
+                        own += io;
+                        if (!in) continue;
+                        if (DIRECT) {
+                            if (direct && r0 + cnt < (unsigned long long)a.max_pairs) a.col[r0 + cnt] = j | kk;
+                        } else if (cnt < (uint32_t)kRowCap) {
+                            row[cnt] = j | kk;
+                        }
+                        cnt++;
+                    }
                 }
             }
         }
@@ -156,197 +476,108 @@ __device__ __forceinline__ uint32_t search_row(const NbArgs& a, int64_t i, int g
     return cnt;
 }
 
-template <int TPP>
-__device__ __forceinline__ uint32_t group_sum_u32(uint32_t v, unsigned gmask)
+__global__ void __launch_bounds__(32 * kNbWarps) k_nb_thread(NbArgs a)
 {
-#pragma unroll
-    for (int o = TPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* total, uint32_t* sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t inc = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    if (lane == 31) sh[warp] = inc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int w = 0; w < nw; w++) {
-            const uint32_t c = sh[w];
-            sh[w] = run;
-            run += c;
-        }
-        sh[32] = run;
-    }
-    __syncthreads();
-    const uint32_t r = inc - v + sh[warp];
-    *total = sh[32];
-    __syncthreads();
-    return r;
-}
-
-template <int TPP>
-__global__ void __launch_bounds__(kNbThreads) k_nb_single(NbArgs a)
-{
-    constexpr int PPT = kNbThreads / TPP;          // particles per tile
-    constexpr int CAP = kNbSmemWords / PPT;        // staged row capacity
-    __shared__ uint32_t s_list[kNbSmemWords];
-    __shared__ uint32_t s_len[PPT];
-    __shared__ uint32_t s_loc[PPT];
-    __shared__ uint32_t s_scan[33];
-    __shared__ uint32_t s_tile;
-    __shared__ unsigned long long s_base;
+    extern __shared__ __align__(16) unsigned char nb_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    NbWarpSmem& S = ((NbWarpSmem*)nb_smem)[warp];
     if (*a.status & kStBad) return;
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (TPP - 1);
-    const unsigned gmask = TPP == 32 ? 0xffffffffu : (((1u << TPP) - 1u) << (lane & ~(TPP - 1)));
-    const unsigned ltmask = (1u << lane) - 1u;
-    const int slot = threadIdx.x / TPP;
-    const int64_t ntiles = (a.n + PPT - 1) / PPT;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-        __syncthreads();
-        const int64_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const int64_t i = tile * PPT + slot;
-        uint32_t own = 0, len = 0;
-        if (i < a.n) {
-            uint32_t* row = s_list + slot * CAP;
-            len = search_row<TPP>(a, i, gl, gmask, ltmask, own, [&](uint32_t pos, uint32_t w) {
-                if (pos < (uint32_t)CAP) row[pos] = w;
-            });
+    for (int64_t q = (int64_t)blockIdx.x * kNbWarps + warp; q < a.nunits; q += (int64_t)gridDim.x * kNbWarps) {
+        const WorkItem U = a.units[q];
+        const PatchDev* P = a.pd + U.patch;
+        const int64_t i = U.begin + lane;
+        const bool act = i < U.end;
+        uint32_t cnt = 0, own = 0;
+        if (act) cnt = thread_walk<false>(a, P, i, S.rows + lane * kRowStride, false, 0, own);
+        const uint32_t v = act ? cnt : 0u;
+        uint32_t inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
         }
-        own = group_sum_u32<TPP>(own, gmask);
-        if (gl == 0) {
-            s_len[slot] = len;
-            if (i < a.n) {
-                a.cnt[i] = len;
-                a.nown[i] = own;
-                if (len > (uint32_t)CAP) a.fix_list[atomicAdd(a.fix_count, 1u)] = (uint32_t)i;
+        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+        unsigned long long base = 0;
+        if (lane == 0) {
+            base = atomicAdd(a.pool_used, (unsigned long long)tot);
+            if (base + tot > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned long long r0 = base + (inc - v);
+        const bool fits = base + tot <= (unsigned long long)a.max_pairs;
+        if (act) {
+            a.rowstart[i] = r0;
+            a.cnt[i] = cnt;
+            a.nown[i] = own;
+        }
+        __syncwarp();
+        if (fits) {
+            const unsigned actm = __ballot_sync(0xffffffffu, act);
+            for (int l = 0; l < 32; l++) {
+                if (!((actm >> l) & 1u)) continue;
+                const uint32_t len = min(__shfl_sync(0xffffffffu, cnt, l), (uint32_t)kRowCap);
+                const unsigned long long rs = __shfl_sync(0xffffffffu, r0, l);
+                for (uint32_t k = lane; k < len; k += 32) a.col[rs + k] = S.rows[l * kRowStride + k];
+            }
+            const bool direct = act && cnt > (uint32_t)kRowCap;
+            if (direct) {
+                uint32_t own2 = 0;
+                thread_walk<true>(a, P, i, nullptr, true, r0, own2);
             }
         }
-        __syncthreads();
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan_u32(threadIdx.x < PPT ? s_len[threadIdx.x] : 0u, &tot, s_scan);
-        if (threadIdx.x < PPT) s_loc[threadIdx.x] = ex;
-        if (threadIdx.x == 0) {
-            // decoupled look-back: publish the tile sum, add predecessors' sums
-            // until one with an inclusive prefix is found
-            atomicExch(a.tile_state + tile, kFlagAgg | (unsigned long long)tot);
-            unsigned long long excl = 0;
-            long long spins = 0;
-            bool ok = true;
-            for (int64_t t = tile - 1; t >= 0;) {
-                const unsigned long long w = *((volatile unsigned long long*)(a.tile_state + t));
-                if ((w >> 62) == 0ull) {
-                    if (++spins > kSpinLimit) {
-                        ok = false;
-                        break;
-                    }
-                    continue;
-                }
-                excl += w & kValMask;
-                if ((w & kFlagPrefix) && !(w & kFlagAgg)) break;
-                t--;
-            }
-            if (!ok) atomicOr(a.status, kStTimeout);
-            atomicExch(a.tile_state + tile, kFlagPrefix | ((excl + tot) & kValMask));
-            s_base = excl;
-            if (tile == ntiles - 1) a.off_w[a.n] = excl + tot;
-            if (excl + tot > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
-        }
-        __syncthreads();
-        const unsigned long long base = s_base;
-        const bool write = !(*((volatile int*)a.status) & (kStOverflow | kStTimeout));
-        if (threadIdx.x < PPT && tile * PPT + threadIdx.x < a.n)
-            a.off_w[tile * PPT + threadIdx.x] = base + s_loc[threadIdx.x];
-        if (write) {
-            // one warp per row, consecutive rows are adjacent in col[]
-            const int warp = threadIdx.x >> 5, nw = kNbThreads >> 5;
-            for (int p = warp; p < PPT; p += nw) {
-                const uint32_t L = min(s_len[p], (uint32_t)CAP);
-                const unsigned long long r0 = base + s_loc[p];
-                for (uint32_t k = lane; k < L; k += 32) a.col[r0 + k] = s_list[p * CAP + k];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// rows that did not fit their shared-memory slot: search again, write whole row
-template <int TPP>
-__global__ void __launch_bounds__(256) k_nb_fixup(NbArgs a)
-{
-    if (*a.status & kStBad) return;
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (TPP - 1);
-    const unsigned gmask = TPP == 32 ? 0xffffffffu : (((1u << TPP) - 1u) << (lane & ~(TPP - 1)));
-    const unsigned ltmask = (1u << lane) - 1u;
-    const uint32_t count = *a.fix_count;
-    const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
-    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; q < count; q += gs) {
-        const int64_t i = a.fix_list[q];
-        const unsigned long long r0 = a.off_w[i];
-        uint32_t own = 0;
-        search_row<TPP>(a, i, gl, gmask, ltmask, own, [&](uint32_t pos, uint32_t w) {
-            if (r0 + pos < (unsigned long long)a.max_pairs) a.col[r0 + pos] = w;
-        });
+        __syncwarp();
     }
 }
 
 int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp)
 {
-    if (a.n <= 0) {
-        cudaMemsetAsync(a.off_w, 0, sizeof(uint64_t), L.stream);
-        return 0;
+    if (a.n <= 0 || a.nunits <= 0) return 0;
+    if (tpp == 1) {
+        const size_t smem = sizeof(NbWarpSmem) * kNbWarps;
+        static bool attr1 = false;
+        if (!attr1) {
+            cudaFuncSetAttribute(k_nb_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr1 = true;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_thread, 32 * kNbWarps, smem);
+        if (per_sm < 1) per_sm = 1;
+        k_nb_thread<<<L.sms * per_sm, 32 * kNbWarps, smem, L.stream>>>(a);
+        return 1;
     }
-    const int grid = L.sms * 6;
-    switch (tpp) {
-    case 1: k_nb_single<1><<<grid, kNbThreads, 0, L.stream>>>(a); break;
-    case 2: k_nb_single<2><<<grid, kNbThreads, 0, L.stream>>>(a); break;
-    case 4: k_nb_single<4><<<grid, kNbThreads, 0, L.stream>>>(a); break;
-    case 16: k_nb_single<16><<<grid, kNbThreads, 0, L.stream>>>(a); break;
-    case 32: k_nb_single<32><<<grid, kNbThreads, 0, L.stream>>>(a); break;
-    default: k_nb_single<8><<<grid, kNbThreads, 0, L.stream>>>(a); break;
+    const size_t smem = sizeof(NbWarpSmem) * kNbWarps;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_nb_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
     }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_warp, 32 * kNbWarps, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_nb_warp<<<L.sms * per_sm, 32 * kNbWarps, smem, L.stream>>>(a);
     return 1;
 }
 
-int launch_nb_fixup(const Launch& L, const NbArgs& a, int tpp)
+// canonical CSR: row i of the pool, columns without the stencil bits, to
+// out[off[i] ..]; one warp per row
+__global__ void k_canonical_rows(int64_t n, const unsigned long long* rowstart, const uint32_t* cnt,
+                                 const uint64_t* off, const uint32_t* col, uint32_t* out)
 {
-    if (a.n <= 0) return 0;
-    const int grid = L.sms * 2;
-    switch (tpp) {
-    case 1: k_nb_fixup<1><<<grid, 256, 0, L.stream>>>(a); break;
-    case 2: k_nb_fixup<2><<<grid, 256, 0, L.stream>>>(a); break;
-    case 4: k_nb_fixup<4><<<grid, 256, 0, L.stream>>>(a); break;
-    case 16: k_nb_fixup<16><<<grid, 256, 0, L.stream>>>(a); break;
-    case 32: k_nb_fixup<32><<<grid, 256, 0, L.stream>>>(a); break;
-    default: k_nb_fixup<8><<<grid, 256, 0, L.stream>>>(a); break;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const unsigned long long r0 = rowstart[i];
+        const uint64_t o = off[i];
+        for (uint32_t k = lane; k < cnt[i]; k += 32) out[o + k] = col[r0 + k] & kColMask;
     }
-    return 1;
 }
 
-int64_t nb_tile_words(int64_t n) { return n / 4 + 16; }
-
-__global__ void k_unpack_cols(int64_t nnz, const uint32_t* col, uint32_t* out)
+int launch_canonical_rows(const Launch& L, int64_t n, const unsigned long long* rowstart,
+                          const uint32_t* cnt, const uint64_t* off, const uint32_t* col, uint32_t* out)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
-         k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = col[k] & kColMask;
-}
-
-int launch_unpack_cols(const Launch& L, int64_t nnz, const uint32_t* col, uint32_t* out)
-{
-    if (nnz <= 0) return 0;
-    int64_t blocks = (nnz + 255) / 256;
+    if (n <= 0) return 0;
+    int64_t blocks = (n * 32 + 255) / 256;
     if (blocks > (int64_t)L.sms * 16) blocks = (int64_t)L.sms * 16;
-    k_unpack_cols<<<(unsigned)blocks, 256, 0, L.stream>>>(nnz, col, out);
+    k_canonical_rows<<<(unsigned)blocks, 256, 0, L.stream>>>(n, rowstart, cnt, off, col, out);
     return 1;
 }
 

@@ -36,6 +36,15 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
     s = t;
 }
 
+// Kahan step for the term a*b: the product is rounded once, inside y
+__device__ __forceinline__ void kahan_fma(float& s, float& c, float a, float b)
+{
+    const float y = fmaf(a, b, -c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
 // merge another lane's compensated sum (value s2 - c2) into (s, c)
 __device__ __forceinline__ void kahan_merge(float& s, float& c, float s2, float c2)
 {
@@ -119,30 +128,42 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
         const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
         const int zmode = P->zmode;
         const float4 ri = a.r.r5[i];
-        const float hf = (float)a.s.h[i];
-        const float inv2h = 0.5f / hf;
-        const uint64_t b = a.off[i], e = a.off[i + 1];
+        const float inv2h = a.r.rv[i].w;                   // 1 / (2 h_i)
+        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
         float sum = 0.0f, comp = 0.0f;
-        for (uint64_t k = b + G.gl; k < e; k += TPP) {
-            const uint32_t cw = a.col[k];
-            const float4 q = a.r.r5[cw & kColMask];
-            const float4 st = tab[cw >> kColBits];
-            float dx, dy, dz;
-            rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float r = r2 * rsqrtf(r2 + 1e-30f);
-            const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
-            const float q2 = qv * qv;
-            kahan_add(sum, comp, q.w * (q2 * q2 * fmaf(-4.0f, qv, 5.0f)));
+        // four neighbours per lane and iteration: the gathers are issued together
+        for (uint64_t k = b + G.gl; k < e; k += 4 * TPP) {
+            uint32_t cw[4];
+            float4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint64_t ku = k + (uint64_t)u * TPP;
+                cw[u] = ku < e ? a.col[ku] : a.col[k];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) q[u] = a.r.r5[cw[u] & kColMask];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const float4 st = tab[cw[u] >> kColBits];
+                float dx, dy, dz;
+                rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float r = r2 * rsqrtf(r2 + 1e-30f);
+                const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
+                const float q2 = qv * qv;
+                const float m = k + (uint64_t)u * TPP < e ? q[u].w : 0.0f;
+                kahan_fma(sum, comp, m, q2 * q2 * fmaf(-4.0f, qv, 5.0f));
+            }
         }
         group_kahan_reduce<TPP>(sum, comp, G.gmask);
         if (G.gl == 0) {
-            const float tot = (float)((double)ri.w + ((double)sum - (double)comp));
-            const float rho = kSigmaWf * tot / (hf * hf * hf);
-            const float u = (float)a.s.u[i];
+            const float tot = ri.w + (sum - comp);           // self term m_i W(0) ~ m_i
+            const float rho = kSigmaWf * tot * (8.0f * inv2h * inv2h * inv2h);
+            const float u = a.r.uf[i];                       // specific energy, staged by the gather
             const float Pr = (gam - 1.0f) * rho * u;
             const float c = sqrtf(gam * Pr / rho);
             const float A = Pr / (rho * rho);
+            const float hf = 0.5f / inv2h;
             a.r.rt[i] = make_float4(rho, A, c, hf);
             a.r.pf[i] = Pr;
             a.r.hc[i] = hf / c;
@@ -166,7 +187,7 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
         const double lz = P->lz, hl = 0.5 * P->lz;
         const double xi = a.s.x[i], yi = a.s.y[i], zi = a.s.z[i], hi = a.s.h[i];
         const double w = 0.5 * a.f.invh[i];
-        const uint64_t b = a.off[i], e = a.off[i + 1];
+        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
         double sum = 0.0;
         for (uint64_t k = b + G.gl; k < e; k += TPP) {
             const uint32_t j = a.col[k] & kColMask;
@@ -198,6 +219,44 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
 // ---------------------------------------------------------------------------
 // A7, mixed precision
 // ---------------------------------------------------------------------------
+struct PairTerms {
+    float ax, ay, az, du;
+};
+
+// one pair of the momentum and energy sums; g scales the whole contribution
+// (m_j, or 0 for a padding lane)
+__device__ __forceinline__ PairTerms momentum_pair(const float4& st, int zmode, float s_f, float sz_f,
+                                                   float lz_f, const float4& ri, const float4& vi,
+                                                   const float4& ti, float wi5, const float4& q,
+                                                   const float4& vj, const float4& tj, float mj,
+                                                   float alpha, float beta, float eps)
+{
+    float dx, dy, dz;
+    rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float r = r2 * rsqrtf(r2 + 1e-30f);
+    const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
+    const float qj = fmaxf(fmaf(-r, vj.w, 1.0f), 0.0f);
+    const float wj2 = vj.w * vj.w;
+    const float wj5 = wj2 * wj2 * vj.w;
+    const float F = fmaf(wj5, qj * qj * qj, wi5 * (qi * qi * qi));
+    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+    const float vdot = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+    const float hbar = 0.5f * (ti.w + tj.w);
+    const float mu = __fdividef(hbar * vdot, fmaf(eps * hbar, hbar, r2));
+    const float pi_ = vdot < 0.0f
+                          ? __fdividef(mu * fmaf(beta, mu, -alpha * 0.5f * (ti.z + tj.z)), 0.5f * (ti.x + tj.x))
+                          : 0.0f;
+    const float g = mj * F;
+    const float fa = g * (ti.y + tj.y + pi_);
+    PairTerms t;
+    t.ax = fa * dx;
+    t.ay = fa * dy;
+    t.az = fa * dz;
+    t.du = -g * fmaf(0.5f, pi_, ti.y) * vdot;
+    return t;
+}
+
 template <int TPP>
 __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
 {
@@ -214,10 +273,9 @@ __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
         const float4 ri = a.r.r5[i];
         const float4 vi = a.r.rv[i];
         const float4 ti = a.r.rt[i];
-        const float wi = vi.w;
-        const float wi2 = wi * wi;
-        const float wi5 = wi2 * wi2 * wi;
-        const uint64_t b = a.off[i], e = a.off[i + 1];
+        const float wi2 = vi.w * vi.w;
+        const float wi5 = wi2 * wi2 * vi.w;
+        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
         float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f;
         for (uint64_t k = b + G.gl; k < e; k += TPP) {
             const uint32_t cw = a.col[k];
@@ -225,40 +283,20 @@ __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
             const float4 q = a.r.r5[j];
             const float4 vj = a.r.rv[j];
             const float4 tj = a.r.rt[j];
-            const float4 st = tab[cw >> kColBits];
-            float dx, dy, dz;
-            rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float r = r2 * rsqrtf(r2 + 1e-30f);
-            const float qi = fmaxf(fmaf(-r, wi, 1.0f), 0.0f);
-            const float qj = fmaxf(fmaf(-r, vj.w, 1.0f), 0.0f);
-            const float wj2 = vj.w * vj.w;
-            const float wj5 = wj2 * wj2 * vj.w;
-            const float F = fmaf(wj5, qj * qj * qj, wi5 * (qi * qi * qi));
-            const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-            const float vdot = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-            const float hbar = 0.5f * (ti.w + tj.w);
-            const float mu = __fdividef(hbar * vdot, fmaf(eps * hbar, hbar, r2));
-            const float pi_ = vdot < 0.0f
-                                  ? __fdividef(mu * fmaf(beta, mu, -alpha * 0.5f * (ti.z + tj.z)),
-                                               0.5f * (ti.x + tj.x))
-                                  : 0.0f;
-            const float g = q.w * F;
-            const float fa = g * (ti.y + tj.y + pi_);
-            kahan_add(sx, cx, fa * dx);
-            kahan_add(sy, cy, fa * dy);
-            kahan_add(sz, cz, fa * dz);
-            kahan_add(su, cu, -g * fmaf(0.5f, pi_, ti.y) * vdot);
+            const PairTerms t = momentum_pair(tab[cw >> kColBits], zmode, s_f, sz_f, lz_f, ri, vi, ti, wi5, q,
+                                              vj, tj, q.w, alpha, beta, eps);
+            kahan_add(sx, cx, t.ax);
+            kahan_add(sy, cy, t.ay);
+            kahan_add(sz, cz, t.az);
+            kahan_add(su, cu, t.du);
         }
         group_kahan_reduce<TPP>(sx, cx, G.gmask);
         group_kahan_reduce<TPP>(sy, cy, G.gmask);
         group_kahan_reduce<TPP>(sz, cz, G.gmask);
         group_kahan_reduce<TPP>(su, cu, G.gmask);
         if (G.gl == 0) {
-            const float4 r = make_float4(k80Sigma * (float)((double)sx - (double)cx),
-                                         k80Sigma * (float)((double)sy - (double)cy),
-                                         k80Sigma * (float)((double)sz - (double)cz),
-                                         k80Sigma * (float)((double)su - (double)cu));
+            const float4 r = make_float4(k80Sigma * (sx - cx), k80Sigma * (sy - cy), k80Sigma * (sz - cz),
+                                         k80Sigma * (su - cu));
             a.r.acc[i] = r;
             if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(r.z) || !isfinite(r.w))
                 atomicOr(a.status, kStNonFinite);
@@ -284,7 +322,7 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
         const double hi = a.s.h[i], wi = 0.5 * a.f.invh[i];
         const double wi5 = wi * wi * wi * wi * wi;
         const double rhoi = a.f.rho[i], Ai = a.f.A[i], ci = a.f.c[i];
-        const uint64_t b = a.off[i], e = a.off[i + 1];
+        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
         double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0;
         for (uint64_t k = b + G.gl; k < e; k += TPP) {
             const uint32_t j = a.col[k] & kColMask;

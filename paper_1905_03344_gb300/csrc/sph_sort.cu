@@ -311,6 +311,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* in, int64
 
 int64_t scan_tmp_words(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
+int launch_scan_u32_to_u64(const Launch& L, int64_t n, const uint32_t* in, uint64_t* out, uint64_t* tmp)
+{
+    if (n <= 0) {
+        cudaMemsetAsync(out, 0, sizeof(uint64_t), L.stream);
+        return 0;
+    }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_reduce<uint32_t, uint64_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp);
+    k_scan_spine<uint64_t><<<1, 1024, 0, L.stream>>>(tmp, nb);
+    k_scan_down<uint32_t, uint64_t><<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, tmp, out, 1);
+    return 3;
+}
+
 static int scan_u32(const Launch& L, int64_t n, const uint32_t* in, uint32_t* out, uint32_t* tmp)
 {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
@@ -500,6 +513,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
         if (mixed) {
             r.r5[k] = make_float4(ox, oy, oz, (float)m);
             r.rv[k] = make_float4((float)vhx, (float)vhy, (float)vhz, 0.5f / hf);
+            r.uf[k] = (float)dst.u[k];
         } else {
             f.vhx[k] = vhx;
             f.vhy[k] = vhy;

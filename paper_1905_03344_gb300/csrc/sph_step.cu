@@ -264,12 +264,6 @@ __global__ void k_unpermute_u32(int64_t n, const uint32_t* src, const uint32_t* 
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         dst[perm[k]] = (double)src[k];
 }
-__global__ void k_row_lengths(int64_t n, const uint64_t* off, const uint32_t* perm, double* dst)
-{
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        dst[perm[k]] = (double)(off[k + 1] - off[k]);
-}
-
 int launch_unpermute_f64(const Launch& L, int64_t n, const double* src, const uint32_t* perm, double* dst)
 {
     if (n <= 0) return 0;
@@ -289,13 +283,6 @@ int launch_unpermute_u32(const Launch& L, int64_t n, const uint32_t* src, const 
     k_unpermute_u32<<<grid_n(L, n), 256, 0, L.stream>>>(n, src, perm, dst);
     return 1;
 }
-int launch_row_lengths(const Launch& L, int64_t n, const uint64_t* off, const uint32_t* perm, double* dst)
-{
-    if (n <= 0) return 0;
-    k_row_lengths<<<grid_n(L, n), 256, 0, L.stream>>>(n, off, perm, dst);
-    return 1;
-}
-
 // inputs must be finite, with m > 0 and h > 0
 __global__ void k_validate(int64_t n, State s, int* status)
 {
