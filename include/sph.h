@@ -224,6 +224,30 @@ sph_status sph_get_nnz(sph_ctx* ctx, int64_t* nnz);
  * reset (the pair-interaction count of the steps); reset != 0 zeroes it. */
 sph_status sph_get_pair_count(sph_ctx* ctx, int64_t* total, int reset);
 
+/* Conserved sums { M, Px, Py, Pz, Lz, Ekin, Eint } (as sph_conserved) of n
+ * particles whose fields the caller already holds on the device, computed
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code that runs
+ * while a stream is being captured into a CUDA graph, host frameworks that
+ * own the device allocator and forbid other allocations, processes that have
+ * handed all device memory to their own pool.
+ * Arguments: device pointers x, y, vx, vy, vz, m, u (n doubles each) and out
+ * (7 doubles, device); cuda_stream is a cudaStream_t or NULL (default
+ * stream).  The call is asynchronous on that stream: read out after
+ * synchronising it.  No context is needed.
+ * Scratch: a fixed array of 4096 partial-sum slots in the library's own
+ * device memory (256 KB, kept by every GPU that loads the library until the
+ * process exits), so n is limited to 16,777,216; larger n returns
+ * SPH_EINVAL.  The first call on a device looks up the array's device
+ * address (do that first call before any stream capture).  Every call
+ * overwrites the array: calls whose work overlaps on the GPU race.
+ * Errors: SPH_EINVAL (n out of range, NULL pointer), SPH_ECUDA;
+ * sph_noalloc_last_error() gives the message. */
+sph_status sph_conserved_noalloc(int64_t n, const double* x, const double* y, const double* vx,
+                                 const double* vy, const double* vz, const double* m,
+                                 const double* u, double* out, void* cuda_stream);
+const char* sph_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,8 @@ SIGNATURES = {
     "sph_get_launch_count": (_ST, [_P, ctypes.POINTER(_I64)]),
     "sph_get_nnz": (_ST, [_P, ctypes.POINTER(_I64)]),
     "sph_get_pair_count": (_ST, [_P, ctypes.POINTER(_I64), ctypes.c_int]),
+    "sph_conserved_noalloc": (_ST, [_I64] + [_P] * 8 + [_P]),
+    "sph_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -294,6 +296,23 @@ def sph_get_pair_count(ctx, reset=False):
     v = ctypes.c_int64()
     _check(ctx, lib().sph_get_pair_count(ctx, ctypes.byref(v), int(bool(reset))))
     return v.value
+
+
+def sph_conserved_noalloc(fields, out, stream=None):
+    """Conserved sums of device arrays without any allocation: fields holds
+    x y vx vy vz m u as float64 CUDA tensors of equal length, out is a
+    float64 CUDA tensor of 7 elements; asynchronous on stream (a CUDA stream
+    handle or None)."""
+    names = ["x", "y", "vx", "vy", "vz", "m", "u"]
+    arrs = [fields[k] for k in names]
+    n = len(arrs[0])
+    for a in arrs + [out]:
+        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
+            raise ValueError("sph_conserved_noalloc takes contiguous CUDA tensors")
+    st = lib().sph_conserved_noalloc(n, *[ctypes.c_void_p(a.data_ptr()) for a in arrs],
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
+    if st != SPH_OK:
+        raise SphError(st, lib().sph_noalloc_last_error().decode())
 
 
 # ---- object wrapper -----------------------------------------------------------
