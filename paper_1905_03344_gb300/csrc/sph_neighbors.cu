@@ -365,12 +365,13 @@ __global__ void __launch_bounds__(32 * kNbWarps) k_nb_warp(NbArgs a)
 // stages its row in shared memory like the warp-tile kernel.
 // DIRECT: lanes with direct = true write their whole row to the pool at r0.
 // ---------------------------------------------------------------------------
-template <bool DIRECT>
-__device__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t* row, bool direct,
-                                unsigned long long r0, uint32_t& own)
+template <bool DIRECT, int K, int ZW>
+__device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t* row, bool direct,
+                                  unsigned long long r0, uint32_t& own)
 {
+    constexpr int NX = 2 * K + 1;
     const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
-    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz, K = P->K, zmode = P->zmode;
+    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
     const uint32_t cbase = (uint32_t)P->cell_base;
     const float4 ri = a.r4[i];
     const uint32_t cc = a.g.cellxyz[i];
@@ -382,54 +383,65 @@ __device__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, u
     const float slack = (1.0f / 4096.0f) * s_f;
     const float Rg = 2.0f * fmaxf(hf, P->hmax_f) * (1.0f + 1.0f / 512.0f) + slack;
     const float Rg2 = Rg * Rg;
+    const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
+    // squared gaps to the cells along x, and their validity, computed once
+    float gx2[NX];
+    bool vx[NX];
+#pragma unroll
+    for (int t = 0; t < NX; t++) {
+        const int d = t - K;
+        const float g = d > 0 ? (float)d * s_f - ri.x : (d < 0 ? ri.x - (float)(d + 1) * s_f : 0.0f);
+        const float gg = fmaxf(g, 0.0f);
+        gx2[t] = gg * gg;
+        vx[t] = (unsigned)(cx + d) < (unsigned)ncx;
+    }
     uint32_t cnt = 0;
-    const int nz = zmode ? ncz : 2 * K + 1;
+    const int nz = ZW ? ncz : NX;
     for (int iz = 0; iz < nz; iz++) {
         int czj, zd;
-        float zsh, gz;
-        if (zmode == 0) {
+        float zsh, gz2;
+        if (!ZW) {
             const int dcz = iz - K;
             czj = cz + dcz;
             if (czj < 0) czj += ncz;
             else if (czj >= ncz) czj -= ncz;
             zsh = (float)dcz * sz_f;
             const float g = dcz > 0 ? (float)dcz * sz_f - ri.z : (dcz < 0 ? ri.z - (float)(dcz + 1) * sz_f : 0.0f);
-            gz = fmaxf(g, 0.0f);
+            const float gg = fmaxf(g, 0.0f);
+            gz2 = gg * gg;
             zd = dcz + 2;
         } else {
             czj = cz + iz;
             if (czj >= ncz) czj -= ncz;
             zsh = (float)iz * sz_f;
-            gz = 0.0f;
+            gz2 = 0.0f;
             zd = iz;
         }
-        const float gz2 = gz * gz;
         if (gz2 >= Rg2) continue;
         const float zo = ri.z - zsh;
         for (int dcy = -K; dcy <= K; dcy++) {
             const int cyj = cy + dcy;
-            if (cyj < 0 || cyj >= ncy) continue;
+            if ((unsigned)cyj >= (unsigned)ncy) continue;
             const float g = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : 0.0f);
             const float gy = fmaxf(g, 0.0f);
             const float gzy2 = fmaf(gy, gy, gz2);
             if (gzy2 >= Rg2) continue;
             const float yo = ri.y - (float)dcy * s_f;
-            for (int dcx = -K; dcx <= K; dcx++) {
-                const int cxj = cx + dcx;
-                if (cxj < 0 || cxj >= ncx) continue;
-                const float gg = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : 0.0f);
-                const float gx = fmaxf(gg, 0.0f);
-                const float d2 = fmaf(gx, gx, gzy2);
-                if (d2 >= Rg2) continue;
-                const uint32_t lin =
-                    cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cxj;
+            const uint32_t lrow = cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cx;
+            const uint32_t kkrow = (uint32_t)(2 + 5 * (dcy + 2) + 25 * zd);
+#pragma unroll
+            for (int t = 0; t < NX; t++) {
+                const int dcx = t - K;
+                const float d2 = gx2[t] + gzy2;
+                if (!vx[t] || d2 >= Rg2) continue;
+                const uint32_t lin = lrow + (uint32_t)dcx;
                 const uint2 se = a.g.cse[lin];
                 const float hc = a.g.chmax[lin];
                 if (se.x >= se.y) continue;
-                const float R = 2.0f * fmaxf(hf, hc) * (1.0f + 1.0f / 512.0f) + slack;
+                const float R = fmaxf(hf, hc) * Rc + slack;
                 if (d2 >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
-                const uint32_t kk = (uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd) << kColBits;
+                const uint32_t kk = (kkrow + (uint32_t)dcx) << kColBits;
                 // four candidates per iteration: the gathers are in flight together
                 for (uint32_t jb = se.x; jb < se.y; jb += 4) {
                     float4 q[4];
@@ -441,17 +453,17 @@ __device__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, u
                     for (int u = 0; u < 4; u++) {
                         const float dx = xo - q[u].x, dy = yo - q[u].y;
                         float dz = zo - q[u].z;
-                        if (zmode) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
+                        if (ZW) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
                         r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         T[u] = fmaxf(Ti, q[u].w);
-                        const uint32_t j = jb + (uint32_t)u;
-                        if (j < se.y && r2[u] <= T[u] * fhi && (int64_t)j != i) near |= 1u << u;
+                        if (jb + (uint32_t)u < se.y && r2[u] <= T[u] * fhi) near |= 1u << u;
                     }
                     if (!near) continue;
 #pragma unroll
                     for (int u = 0; u < 4; u++) {
                         if (!(near & (1u << u))) continue;
                         const uint32_t j = jb + (uint32_t)u;
+                        if ((int64_t)j == i) continue;
                         bool in = r2[u] < T[u] * flo;
                         bool io = r2[u] < Ti * flo;
                         if (!in || (!io && r2[u] <= Ti * fhi)) {
@@ -474,6 +486,18 @@ __device__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, u
         }
     }
     return cnt;
+}
+
+template <bool DIRECT>
+__device__ __forceinline__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t* row,
+                                                bool direct, unsigned long long r0, uint32_t& own)
+{
+    if (P->zmode) {
+        if (P->K == 1) return thread_walk_k<DIRECT, 1, 1>(a, P, i, row, direct, r0, own);
+        return thread_walk_k<DIRECT, 2, 1>(a, P, i, row, direct, r0, own);
+    }
+    if (P->K == 1) return thread_walk_k<DIRECT, 1, 0>(a, P, i, row, direct, r0, own);
+    return thread_walk_k<DIRECT, 2, 0>(a, P, i, row, direct, r0, own);
 }
 
 __global__ void __launch_bounds__(32 * kNbWarps) k_nb_thread(NbArgs a)

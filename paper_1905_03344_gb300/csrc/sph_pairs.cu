@@ -97,15 +97,17 @@ __device__ __forceinline__ GroupIdx group_idx()
     return g;
 }
 
-// pair separation x_i - x_j from cell-relative FP32 coordinates
-__device__ __forceinline__ void rel_dx(const float4& e, int zmode, float s_f, float sz_f, float lz_f,
-                                       float oxi, float oyi, float ozi, const float4& q, float& dx,
-                                       float& dy, float& dz)
+// pair separation x_i - x_j from cell-relative FP32 coordinates; ZW = 1 when
+// the patch has fewer than 2K+1 z cells (z offset as a cell count, then the
+// minimum image), ZW = 0 otherwise (signed z offset, no wrap needed)
+template <int ZW>
+__device__ __forceinline__ void rel_dx(const float4& e, float s_f, float sz_f, float lz_f, float oxi,
+                                       float oyi, float ozi, const float4& q, float& dx, float& dy, float& dz)
 {
     dx = fmaf(-e.x, s_f, oxi - q.x);
     dy = fmaf(-e.y, s_f, oyi - q.y);
-    dz = fmaf(-(zmode ? e.w : e.z), sz_f, ozi - q.z);
-    if (zmode) {
+    dz = fmaf(-(ZW ? e.w : e.z), sz_f, ozi - q.z);
+    if (ZW) {
         if (dz > 0.5f * lz_f) dz -= lz_f;
         else if (dz < -0.5f * lz_f) dz += lz_f;
     }
@@ -114,6 +116,35 @@ __device__ __forceinline__ void rel_dx(const float4& e, int zmode, float s_f, fl
 // ---------------------------------------------------------------------------
 // A5 + A6, mixed precision
 // ---------------------------------------------------------------------------
+// the row of one particle: plain FP32 weights m_j q^4 (5 - 4q), Kahan sum
+template <int TPP, int ZW>
+__device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
+                                            int gl, float s_f, float sz_f, float lz_f, const float4& ri, float inv2h,
+                                            float& sum, float& comp)
+{
+    // four neighbours per lane and iteration: the gathers are issued together
+    for (uint32_t k = gl; k < len; k += 4 * TPP) {
+        uint32_t cw[4];
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cw[u] = row[min(k + (uint32_t)(u * TPP), len - 1u)];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = a.r.r5[cw[u] & kColMask];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float4 st = tab[cw[u] >> kColBits];
+            float dx, dy, dz;
+            rel_dx<ZW>(st, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(r2 + 1e-30f);
+            const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
+            const float q2 = qv * qv;
+            const float m = k + (uint32_t)(u * TPP) < len ? q[u].w : 0.0f;
+            kahan_fma(sum, comp, m, q2 * q2 * fmaf(-4.0f, qv, 5.0f));
+        }
+    }
+}
+
 template <int TPP>
 __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 {
@@ -126,35 +157,13 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
         const PatchDev* P = a.pd + a.patch_of[i];
         const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
-        const int zmode = P->zmode;
         const float4 ri = a.r.r5[i];
         const float inv2h = a.r.rv[i].w;                   // 1 / (2 h_i)
-        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
+        const uint32_t* row = a.col + a.rowstart[i];
+        const uint32_t len = a.cnt[i];
         float sum = 0.0f, comp = 0.0f;
-        // four neighbours per lane and iteration: the gathers are issued together
-        for (uint64_t k = b + G.gl; k < e; k += 4 * TPP) {
-            uint32_t cw[4];
-            float4 q[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const uint64_t ku = k + (uint64_t)u * TPP;
-                cw[u] = ku < e ? a.col[ku] : a.col[k];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) q[u] = a.r.r5[cw[u] & kColMask];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const float4 st = tab[cw[u] >> kColBits];
-                float dx, dy, dz;
-                rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float r = r2 * rsqrtf(r2 + 1e-30f);
-                const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
-                const float q2 = qv * qv;
-                const float m = k + (uint64_t)u * TPP < e ? q[u].w : 0.0f;
-                kahan_fma(sum, comp, m, q2 * q2 * fmaf(-4.0f, qv, 5.0f));
-            }
-        }
+        if (P->zmode) density_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, sum, comp);
+        else density_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, sum, comp);
         group_kahan_reduce<TPP>(sum, comp, G.gmask);
         if (G.gl == 0) {
             const float tot = ri.w + (sum - comp);           // self term m_i W(0) ~ m_i
@@ -187,10 +196,11 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
         const double lz = P->lz, hl = 0.5 * P->lz;
         const double xi = a.s.x[i], yi = a.s.y[i], zi = a.s.z[i], hi = a.s.h[i];
         const double w = 0.5 * a.f.invh[i];
-        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
+        const uint32_t* row = a.col + a.rowstart[i];
+        const uint32_t len = a.cnt[i];
         double sum = 0.0;
-        for (uint64_t k = b + G.gl; k < e; k += TPP) {
-            const uint32_t j = a.col[k] & kColMask;
+        for (uint32_t k = G.gl; k < len; k += TPP) {
+            const uint32_t j = row[k] & kColMask;
             const double dx = xi - a.s.x[j], dy = yi - a.s.y[j];
             double dz = zi - a.s.z[j];
             if (dz > hl) dz -= lz;
@@ -225,14 +235,15 @@ struct PairTerms {
 
 // one pair of the momentum and energy sums; g scales the whole contribution
 // (m_j, or 0 for a padding lane)
-__device__ __forceinline__ PairTerms momentum_pair(const float4& st, int zmode, float s_f, float sz_f,
+template <int ZW>
+__device__ __forceinline__ PairTerms momentum_pair(const float4& st, float s_f, float sz_f,
                                                    float lz_f, const float4& ri, const float4& vi,
                                                    const float4& ti, float wi5, const float4& q,
                                                    const float4& vj, const float4& tj, float mj,
                                                    float alpha, float beta, float eps)
 {
     float dx, dy, dz;
-    rel_dx(st, zmode, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+    rel_dx<ZW>(st, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
     const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
@@ -257,6 +268,31 @@ __device__ __forceinline__ PairTerms momentum_pair(const float4& st, int zmode, 
     return t;
 }
 
+struct MomAcc {
+    float sx, cx, sy, cy, sz, cz, su, cu;
+};
+
+template <int TPP, int ZW>
+__device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
+                                             int gl, float s_f, float sz_f, float lz_f, const float4& ri,
+                                             const float4& vi, const float4& ti, float wi5, float alpha, float beta,
+                                             float eps, MomAcc& A)
+{
+    for (uint32_t k = gl; k < len; k += TPP) {
+        const uint32_t cw = row[k];
+        const uint32_t j = cw & kColMask;
+        const float4 q = a.r.r5[j];
+        const float4 vj = a.r.rv[j];
+        const float4 tj = a.r.rt[j];
+        const PairTerms t = momentum_pair<ZW>(tab[cw >> kColBits], s_f, sz_f, lz_f, ri, vi, ti, wi5, q, vj, tj,
+                                              q.w, alpha, beta, eps);
+        kahan_add(A.sx, A.cx, t.ax);
+        kahan_add(A.sy, A.cy, t.ay);
+        kahan_add(A.sz, A.cz, t.az);
+        kahan_add(A.su, A.cu, t.du);
+    }
+}
+
 template <int TPP>
 __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
 {
@@ -269,34 +305,25 @@ __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
         const PatchDev* P = a.pd + a.patch_of[i];
         const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
-        const int zmode = P->zmode;
         const float4 ri = a.r.r5[i];
         const float4 vi = a.r.rv[i];
         const float4 ti = a.r.rt[i];
         const float wi2 = vi.w * vi.w;
         const float wi5 = wi2 * wi2 * vi.w;
-        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
-        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, su = 0.f, cu = 0.f;
-        for (uint64_t k = b + G.gl; k < e; k += TPP) {
-            const uint32_t cw = a.col[k];
-            const uint32_t j = cw & kColMask;
-            const float4 q = a.r.r5[j];
-            const float4 vj = a.r.rv[j];
-            const float4 tj = a.r.rt[j];
-            const PairTerms t = momentum_pair(tab[cw >> kColBits], zmode, s_f, sz_f, lz_f, ri, vi, ti, wi5, q,
-                                              vj, tj, q.w, alpha, beta, eps);
-            kahan_add(sx, cx, t.ax);
-            kahan_add(sy, cy, t.ay);
-            kahan_add(sz, cz, t.az);
-            kahan_add(su, cu, t.du);
-        }
-        group_kahan_reduce<TPP>(sx, cx, G.gmask);
-        group_kahan_reduce<TPP>(sy, cy, G.gmask);
-        group_kahan_reduce<TPP>(sz, cz, G.gmask);
-        group_kahan_reduce<TPP>(su, cu, G.gmask);
+        const uint32_t* row = a.col + a.rowstart[i];
+        const uint32_t len = a.cnt[i];
+        MomAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (P->zmode)
+            momentum_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, A);
+        else
+            momentum_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, A);
+        group_kahan_reduce<TPP>(A.sx, A.cx, G.gmask);
+        group_kahan_reduce<TPP>(A.sy, A.cy, G.gmask);
+        group_kahan_reduce<TPP>(A.sz, A.cz, G.gmask);
+        group_kahan_reduce<TPP>(A.su, A.cu, G.gmask);
         if (G.gl == 0) {
-            const float4 r = make_float4(k80Sigma * (sx - cx), k80Sigma * (sy - cy), k80Sigma * (sz - cz),
-                                         k80Sigma * (su - cu));
+            const float4 r = make_float4(k80Sigma * (A.sx - A.cx), k80Sigma * (A.sy - A.cy), k80Sigma * (A.sz - A.cz),
+                                         k80Sigma * (A.su - A.cu));
             a.r.acc[i] = r;
             if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(r.z) || !isfinite(r.w))
                 atomicOr(a.status, kStNonFinite);
@@ -322,10 +349,11 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
         const double hi = a.s.h[i], wi = 0.5 * a.f.invh[i];
         const double wi5 = wi * wi * wi * wi * wi;
         const double rhoi = a.f.rho[i], Ai = a.f.A[i], ci = a.f.c[i];
-        const uint64_t b = a.rowstart[i], e = b + a.cnt[i];
+        const uint32_t* row = a.col + a.rowstart[i];
+        const uint32_t len = a.cnt[i];
         double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0;
-        for (uint64_t k = b + G.gl; k < e; k += TPP) {
-            const uint32_t j = a.col[k] & kColMask;
+        for (uint32_t k = G.gl; k < len; k += TPP) {
+            const uint32_t j = row[k] & kColMask;
             const double dx = xi - a.s.x[j], dy = yi - a.s.y[j];
             double dz = zi - a.s.z[j];
             if (dz > hl) dz -= lz;
