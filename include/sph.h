@@ -84,7 +84,11 @@ typedef struct {
     int32_t threads_per_particle; /* 0 = auto; else 1, 2, 4, 8, 16 or 32 */
     double cell_factor;     /* cell edge = 2 h_max * cell_factor, in [0.5, 4] */
     int64_t max_particles;  /* capacity, <= 2^25 */
-    int64_t max_pairs;      /* neighbour-list capacity; 0 = 160 * max_particles */
+    int64_t max_pairs;      /* neighbour-list capacity (total list entries);
+                               0 = 160 * max_particles.  The list pool holds
+                               5/2 max_pairs + 24 max_particles + 64 entries of
+                               4 bytes: rows are reserved ahead of the search
+                               with a margin over their previous length. */
     int32_t max_patches;    /* capacity of independent patches, <= 256 */
     int32_t use_graph;      /* 1: sph_step replays a captured CUDA graph */
     void* cuda_stream;      /* cudaStream_t or NULL */

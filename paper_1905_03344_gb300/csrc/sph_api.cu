@@ -66,7 +66,7 @@ struct sph_ctx {
     std::string err;
     bool poisoned = false;
 
-    int64_t cap_n = 0, max_pairs = 0, cap_cells = 0;
+    int64_t cap_n = 0, max_pairs = 0, pool_cap = 0, cap_cells = 0;
     int cap_patch = 0, cap_items = 0;
     int64_t n = 0;
     int npatch = 0, nitems = 0, radix_passes = 3;
@@ -86,7 +86,9 @@ struct sph_ctx {
     uint32_t *cnt = nullptr, *nown = nullptr, *col = nullptr, *col_plain = nullptr;
     WorkItem* units = nullptr;     // 32-particle warp units, per patch
     int64_t nunits = 0, cap_units = 0;
-    unsigned long long *rowstart = nullptr, *pool_used = nullptr;
+    unsigned long long *rowstart = nullptr, *pool_used = nullptr;  // pool_used: [reserved, listed]
+    uint32_t* rowcap = nullptr;    // row-length hints in the current sorted order
+    int* hint_ok = nullptr;        // device flag: cnt holds row lengths of the current order
     uint64_t* scan64 = nullptr;
     bool canon_valid = false;      // off / col_plain hold the canonical CSR
     int64_t col_plain_cap = 0;
@@ -233,8 +235,10 @@ NbArgs nb_args(sph_ctx* ctx)
     a.nown = ctx->nown;
     a.rowstart = ctx->rowstart;
     a.col = ctx->col;
+    a.rowcap = ctx->rowcap;
     a.pool_used = ctx->pool_used;
     a.max_pairs = ctx->max_pairs;
+    a.pool_cap = ctx->pool_cap;
     a.status = ctx->status;
     a.units = ctx->units;
     a.nunits = ctx->nunits;
@@ -312,7 +316,7 @@ void enqueue_sort(sph_ctx* ctx)
         const int nxt = 1 - ctx->cur;
         ctx->launches += launch_gather(L, ctx->n, ctx->keys, ctx->vals, ctx->st[ctx->cur], ctx->st[nxt],
                                        ctx->perm[ctx->cur], ctx->perm[nxt], ctx->pd, ctx->grid, ctx->rec,
-                                       ctx->f64, ctx->mixed);
+                                       ctx->f64, ctx->mixed, RowHint{ctx->cnt, ctx->hint_ok, ctx->rowcap});
         ctx->cur = nxt;
     }
     ctx->fresh = false;
@@ -324,13 +328,15 @@ void enqueue_lists(sph_ctx* ctx)
     const NbArgs a = nb_args(ctx);
     {
         Phase p(ctx, SPH_PHASE_NB_RESET);
-        cudaMemsetAsync(ctx->pool_used, 0, sizeof(unsigned long long), ctx->stream);
+        cudaMemsetAsync(ctx->pool_used, 0, 2 * sizeof(unsigned long long), ctx->stream);
     }
     ctx->canon_valid = false;
     {
         Phase p(ctx, SPH_PHASE_NB);
-        ctx->launches += launch_nb_lists(L, a, ctx->tpp_nb);
+        ctx->launches += launch_nb_lists(L, a, ctx->tpp_nb, ctx->cell_factor >= 1.0 ? 1 : 2);
     }
+    // the row lengths now belong to the current order: hints for the next sort
+    cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
 }
 
 void enqueue_density(sph_ctx* ctx)
@@ -354,7 +360,7 @@ void enqueue_step(sph_ctx* ctx)
     {
         Phase p(ctx, SPH_PHASE_UPDATE);
         const StepArgs a = step_args(ctx);
-        k_accum_pairs<<<1, 1, 0, ctx->stream>>>(ctx->pool_used, ctx->pair_acc, ctx->status);
+        k_accum_pairs<<<1, 1, 0, ctx->stream>>>(ctx->pool_used + 1, ctx->pair_acc, ctx->status);
         ctx->launches += 1;
         ctx->launches += launch_hc_min(L, a);
         ctx->launches += launch_dt(L, a);
@@ -462,6 +468,8 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
     ctx->patch_off.assign(offsets, offsets + np + 1);
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
     destroy_graphs(ctx);
+    // new particle order: no row-length hints
+    CK(cudaMemsetAsync(ctx->hint_ok, 0, sizeof(int), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return after_launches(ctx, "setup_patches");
 }
@@ -593,6 +601,11 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ctx->cap_n = cfg.max_particles;
     ctx->cap_patch = cfg.max_patches;
     ctx->max_pairs = cfg.max_pairs > 0 ? cfg.max_pairs : 160 * cfg.max_particles;
+    // rows are reserved ahead in multiples of 8 entries, at 4/3 of their
+    // previous length plus 8, and a row that outgrows its reservation takes a
+    // second one: 5/2 max_pairs + 24 per particle holds any step whose lists
+    // fit in max_pairs after a step whose lists did
+    ctx->pool_cap = ctx->max_pairs * 5 / 2 + 24 * cfg.max_particles + 64;
     ctx->cap_items = (int)(ctx->cap_n / kItemChunk + ctx->cap_patch + 1);
     ctx->cap_cells = 2 * ctx->cap_n + (int64_t)4096 * ctx->cap_patch;
     const size_t N = (size_t)ctx->cap_n;
@@ -628,9 +641,9 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         for (int k = 0; k < 13 && ok; k++) ok = dalloc(ctx, *g[k], N);
     }
     ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->nown, N) && dalloc(ctx, ctx->off, N + 1) &&
-         dalloc(ctx, ctx->col, (size_t)ctx->max_pairs);
+         dalloc(ctx, ctx->col, (size_t)ctx->pool_cap) && dalloc(ctx, ctx->rowcap, N);
     ctx->cap_units = ctx->cap_n / 32 + ctx->cap_patch + 1;
-    ok = ok && dalloc(ctx, ctx->rowstart, N) && dalloc(ctx, ctx->pool_used, 1) &&
+    ok = ok && dalloc(ctx, ctx->rowstart, N) && dalloc(ctx, ctx->pool_used, 2) && dalloc(ctx, ctx->hint_ok, 1) &&
          dalloc(ctx, ctx->units, (size_t)ctx->cap_units) &&
          dalloc(ctx, ctx->scan64, (size_t)scan_tmp_words(ctx->cap_n));
     ok = ok && dalloc(ctx, ctx->pd, (size_t)ctx->cap_patch) && dalloc(ctx, ctx->red, (size_t)ctx->cap_patch) &&
@@ -714,7 +727,7 @@ sph_status sph_find_neighbors(sph_ctx* ctx)
     st = after_launches(ctx, "sph_find_neighbors");
     if (st != SPH_OK) return st;
     unsigned long long nnz = 0;
-    CK(cudaMemcpyAsync(&nnz, ctx->pool_used, sizeof(nnz), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&nnz, ctx->pool_used + 1, sizeof(nnz), cudaMemcpyDeviceToHost, ctx->stream));
     st = check_status(ctx, "sph_find_neighbors");
     ctx->nnz = (int64_t)nnz;
     if (st != SPH_OK) return st;

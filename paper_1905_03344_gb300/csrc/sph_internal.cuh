@@ -149,10 +149,19 @@ int launch_keys(const Launch& L, int64_t n, const State& s, const uint16_t* patc
 int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, uint32_t* vals,
                       uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist, uint32_t* scan_tmp);
 size_t radix_hist_words(int64_t n);
+// Row-length hints for the list pool: the previous lists' row lengths,
+// carried into the new sorted order by the gather.  Only a hint: the list
+// kernel reserves from it and repairs rows that outgrow their reservation.
+constexpr uint32_t kNoHint = 0xffffffffu;
+struct RowHint {
+    const uint32_t* cnt_prev;    // row lengths in the previous sorted order
+    const int* valid;            // nonzero: cnt_prev belongs to the order being gathered from
+    uint32_t* rowcap;            // out: hint per new sorted slot, kNoHint if none
+};
 int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint32_t* svals,
                   const State& src, const State& dst, const uint32_t* perm_src,
                   uint32_t* perm_dst, const PatchDev* pd, const Grid& g, const Recs& r,
-                  const Fp64& f, int mixed);
+                  const Fp64& f, int mixed, const RowHint& hint);
 // temporary words of the device-wide exclusive scan over n values
 int64_t scan_tmp_words(int64_t n);
 
@@ -168,11 +177,14 @@ struct NbArgs {
     uint32_t* nown;                      // n_i
     unsigned long long* rowstart;        // first pool entry of row i
     uint32_t* col;                       // the list pool
-    unsigned long long* pool_used;       // entries reserved so far
-    int64_t max_pairs;
+    const uint32_t* rowcap;              // row-length hints (kNoHint: none)
+    unsigned long long* pool_used;       // [0] entries reserved, [1] entries listed (nnz)
+    int64_t max_pairs;                   // bound on nnz
+    int64_t pool_cap;                    // entries the pool holds (max_pairs + slack)
     int* status;
 };
-int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp);
+// K: stencil half-extent of every patch (1 for cell_factor >= 1, else 2)
+int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp, int K);
 int launch_canonical_rows(const Launch& L, int64_t n, const unsigned long long* rowstart,
                           const uint32_t* cnt, const uint64_t* off, const uint32_t* col, uint32_t* out);
 // exclusive scan of n u32 values into u64 out[0..n], out[n] = total

@@ -68,6 +68,13 @@ __device__ __forceinline__ int exact_pair(double xi, double yi, double zi, doubl
     return (own | oth) | (own << 1);
 }
 
+// the same predicate for sorted slots i, j, out of line: it runs only inside
+// the guard band, and one copy keeps the thread walk small
+__device__ __noinline__ int exact_pair_at(const NbArgs& a, int64_t i, uint32_t j, double lz)
+{
+    return exact_pair(a.x[i], a.y[i], a.z[i], a.h[i], a.x[j], a.y[j], a.z[j], a.h[j], lz);
+}
+
 __device__ __forceinline__ float warp_min(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -194,7 +201,7 @@ __device__ void warp_walk(const NbArgs& a, const PatchDev* P, NbWarpSmem& S, Lan
                         w = j | ((uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd) << kColBits);
                     }
                     if (DIRECT) {
-                        if (direct && r0 + L.cnt < (unsigned long long)a.max_pairs) a.col[r0 + L.cnt] = w;
+                        if (direct && r0 + L.cnt < (unsigned long long)a.pool_cap) a.col[r0 + L.cnt] = w;
                     } else if (L.cnt < (uint32_t)kRowCap) {
                         S.rows[lane * kRowStride + L.cnt] = w;
                     }
@@ -323,12 +330,14 @@ __global__ void __launch_bounds__(32 * kNbWarps) k_nb_warp(NbArgs a)
             const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
             unsigned long long base = 0;
             if (lane == 0) {
-                base = atomicAdd(a.pool_used, (unsigned long long)tot);
-                if (base + tot > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
+                base = atomicAdd(&a.pool_used[0], (unsigned long long)tot);
+                const unsigned long long before = atomicAdd(&a.pool_used[1], (unsigned long long)tot);
+                if (base + tot > (unsigned long long)a.pool_cap || before + tot > (unsigned long long)a.max_pairs)
+                    atomicOr(a.status, kStOverflow);
             }
             base = __shfl_sync(0xffffffffu, base, 0);
             const unsigned long long r0 = base + (inc - v);
-            const bool fits = base + tot <= (unsigned long long)a.max_pairs;
+            const bool fits = base + tot <= (unsigned long long)a.pool_cap;
             if (L.act) {
                 a.rowstart[i] = r0;
                 a.cnt[i] = L.cnt;
@@ -361,15 +370,54 @@ __global__ void __launch_bounds__(32 * kNbWarps) k_nb_warp(NbArgs a)
 // ---------------------------------------------------------------------------
 // Thread-per-particle variant: each lane walks the (2K+1)^3 cells around its
 // own cell with its own pruning, in the same loop order as the other lanes of
-// its warp (lanes of one cell load the same candidates at the same time), and
-// stages its row in shared memory like the warp-tile kernel.
-// DIRECT: lanes with direct = true write their whole row to the pool at r0.
+// its warp (lanes of one cell load the same candidates at the same time).
+//
+// Rows go straight to the pool.  Each lane reserves its row before the walk,
+// from the row-length hint c (the particle's row length in the previous
+// lists) as c + c/3 + 8 entries -- on a lattice a small change of h adds a
+// whole shell of neighbours at once, up to about a third of the row -- or,
+// without a hint, from a first walk that only counts.  Reservations are
+// rounded up to a multiple of 8 entries, so every row starts on a 32-byte
+// boundary.  Hits
+// collect in a 16-slot ring in shared memory and leave it as whole 32-byte
+// sectors.  A row that outgrows its reservation is walked again into a fresh
+// reservation of its exact (rounded) length.  Shared memory per warp is 2 KB,
+// which leaves the SM's L1 to the candidate gathers.
 // ---------------------------------------------------------------------------
-template <bool DIRECT, int K, int ZW>
-__device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t* row, bool direct,
-                                  unsigned long long r0, uint32_t& own)
+#ifndef SPH_NB_MINB
+#define SPH_NB_MINB 8                   // resident CTAs per SM the registers are sized for
+#endif
+#ifndef SPH_NB_GROUP
+#define SPH_NB_GROUP 4                  // candidates loaded together per lane
+#endif
+constexpr int kNbtWarps = 4;            // warps per CTA
+constexpr int kGroup = SPH_NB_GROUP;
+static_assert(kGroup >= 1 && kGroup <= 8, "a group may fill at most one half of the ring");
+constexpr int kRing = 16;               // ring slots per lane (two halves of 8)
+constexpr uint32_t kHintMargin = 8;     // growth a row may have since the hint, beyond c/3
+
+enum WalkMode { kWalkCount = 0, kWalkRing = 1, kWalkDirect = 2 };
+
+struct RowOut {
+    uint32_t* col;      // the row's first pool entry
+    uint32_t res;       // entries reserved
+    uint32_t* ring;     // this lane's ring: slot k at ring[32 k]
+};
+
+__device__ __forceinline__ uint32_t round8(uint32_t v) { return (v + 7u) & ~7u; }
+
+// ring half hf (8 entries) to the pool at row entry blk, as two 16-byte stores
+__device__ __forceinline__ void ring_flush(const RowOut& o, uint32_t hf, uint32_t blk)
 {
-    constexpr int NX = 2 * K + 1;
+    const uint32_t* rg = o.ring + hf * (8 * 32);
+    uint4* dst = reinterpret_cast<uint4*>(o.col + blk);
+    dst[0] = make_uint4(rg[0], rg[32], rg[64], rg[96]);
+    dst[1] = make_uint4(rg[128], rg[160], rg[192], rg[224]);
+}
+
+template <int MODE, int K, int ZW>
+__device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i, const RowOut& o, uint32_t& own)
+{
     const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
     const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
     const uint32_t cbase = (uint32_t)P->cell_base;
@@ -384,19 +432,8 @@ __device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i,
     const float Rg = 2.0f * fmaxf(hf, P->hmax_f) * (1.0f + 1.0f / 512.0f) + slack;
     const float Rg2 = Rg * Rg;
     const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
-    // squared gaps to the cells along x, and their validity, computed once
-    float gx2[NX];
-    bool vx[NX];
-#pragma unroll
-    for (int t = 0; t < NX; t++) {
-        const int d = t - K;
-        const float g = d > 0 ? (float)d * s_f - ri.x : (d < 0 ? ri.x - (float)(d + 1) * s_f : 0.0f);
-        const float gg = fmaxf(g, 0.0f);
-        gx2[t] = gg * gg;
-        vx[t] = (unsigned)(cx + d) < (unsigned)ncx;
-    }
     uint32_t cnt = 0;
-    const int nz = ZW ? ncz : NX;
+    const int nz = ZW ? ncz : 2 * K + 1;
     for (int iz = 0; iz < nz; iz++) {
         int czj, zd;
         float zsh, gz2;
@@ -429,11 +466,14 @@ __device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i,
             const float yo = ri.y - (float)dcy * s_f;
             const uint32_t lrow = cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cx;
             const uint32_t kkrow = (uint32_t)(2 + 5 * (dcy + 2) + 25 * zd);
-#pragma unroll
-            for (int t = 0; t < NX; t++) {
-                const int dcx = t - K;
-                const float d2 = gx2[t] + gzy2;
-                if (!vx[t] || d2 >= Rg2) continue;
+            // one copy of the candidate loop for all x offsets (code size)
+#pragma unroll 1
+            for (int dcx = -K; dcx <= K; dcx++) {
+                if ((unsigned)(cx + dcx) >= (unsigned)ncx) continue;
+                const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : 0.0f);
+                const float gx = fmaxf(gxr, 0.0f);
+                const float d2 = fmaf(gx, gx, gzy2);
+                if (d2 >= Rg2) continue;
                 const uint32_t lin = lrow + (uint32_t)dcx;
                 const uint2 se = a.g.cse[lin];
                 const float hc = a.g.chmax[lin];
@@ -442,15 +482,15 @@ __device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i,
                 if (d2 >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
                 const uint32_t kk = (kkrow + (uint32_t)dcx) << kColBits;
-                // four candidates per iteration: the gathers are in flight together
-                for (uint32_t jb = se.x; jb < se.y; jb += 4) {
-                    float4 q[4];
+                // kGroup candidates per iteration: their gathers are in flight together
+                for (uint32_t jb = se.x; jb < se.y; jb += kGroup) {
+                    float4 q[kGroup];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) q[u] = a.r4[min(jb + (uint32_t)u, se.y - 1u)];
-                    float r2[4], T[4];
+                    for (int u = 0; u < kGroup; u++) q[u] = a.r4[min(jb + (uint32_t)u, se.y - 1u)];
+                    float r2[kGroup], T[kGroup];
                     unsigned near = 0;
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
+                    for (int u = 0; u < kGroup; u++) {
                         const float dx = xo - q[u].x, dy = yo - q[u].y;
                         float dz = zo - q[u].z;
                         if (ZW) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
@@ -459,113 +499,147 @@ __device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i,
                         if (jb + (uint32_t)u < se.y && r2[u] <= T[u] * fhi) near |= 1u << u;
                     }
                     if (!near) continue;
+                    const uint32_t c0 = cnt;
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
+                    for (int u = 0; u < kGroup; u++) {
                         if (!(near & (1u << u))) continue;
                         const uint32_t j = jb + (uint32_t)u;
                         if ((int64_t)j == i) continue;
                         bool in = r2[u] < T[u] * flo;
                         bool io = r2[u] < Ti * flo;
                         if (!in || (!io && r2[u] <= Ti * fhi)) {
-                            const int e = exact_pair(a.x[i], a.y[i], a.z[i], a.h[i], a.x[j], a.y[j], a.z[j],
-                                                     a.h[j], P->lz);
+                            const int e = exact_pair_at(a, i, j, P->lz);
                             in = e & 1;
                             io = (e >> 1) & 1;
                         }
                         own += io;
                         if (!in) continue;
-                        if (DIRECT) {
-                            if (direct && r0 + cnt < (unsigned long long)a.max_pairs) a.col[r0 + cnt] = j | kk;
-                        } else if (cnt < (uint32_t)kRowCap) {
-                            row[cnt] = j | kk;
-                        }
+                        if (MODE == kWalkRing) o.ring[(cnt & (kRing - 1)) * 32] = j | kk;
+                        else if (MODE == kWalkDirect) o.col[cnt] = j | kk;
                         cnt++;
+                    }
+                    // at most kGroup <= 8 hits per group: at most one half of the ring filled
+                    if (MODE == kWalkRing && ((c0 ^ cnt) & 8u)) {
+                        const uint32_t blk = c0 & ~7u;
+                        if (blk + 8u <= o.res) ring_flush(o, (blk >> 3) & 1u, blk);
                     }
                 }
             }
         }
     }
+    if (MODE == kWalkRing && cnt <= o.res) {
+        // the partly filled last sector
+        const uint32_t blk = cnt & ~7u;
+        for (uint32_t k = blk; k < cnt; k++) o.col[k] = o.ring[(k & (kRing - 1)) * 32];
+    }
     return cnt;
 }
 
-template <bool DIRECT>
-__device__ __forceinline__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t* row,
-                                                bool direct, unsigned long long r0, uint32_t& own)
+template <int MODE, int K>
+__device__ __forceinline__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, const RowOut& o,
+                                                uint32_t& own)
 {
-    if (P->zmode) {
-        if (P->K == 1) return thread_walk_k<DIRECT, 1, 1>(a, P, i, row, direct, r0, own);
-        return thread_walk_k<DIRECT, 2, 1>(a, P, i, row, direct, r0, own);
-    }
-    if (P->K == 1) return thread_walk_k<DIRECT, 1, 0>(a, P, i, row, direct, r0, own);
-    return thread_walk_k<DIRECT, 2, 0>(a, P, i, row, direct, r0, own);
+    if (P->zmode) return thread_walk_k<MODE, K, 1>(a, P, i, o, own);
+    return thread_walk_k<MODE, K, 0>(a, P, i, o, own);
 }
 
-__global__ void __launch_bounds__(32 * kNbWarps) k_nb_thread(NbArgs a)
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
 {
-    extern __shared__ __align__(16) unsigned char nb_smem[];
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// K: stencil half-extent, the same for every patch (it follows cell_factor)
+template <int K>
+__global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArgs a)
+{
+    extern __shared__ __align__(16) uint32_t nb_ring[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    NbWarpSmem& S = ((NbWarpSmem*)nb_smem)[warp];
+    uint32_t* ring = nb_ring + warp * (32 * kRing) + lane;
     if (*a.status & kStBad) return;
-    for (int64_t q = (int64_t)blockIdx.x * kNbWarps + warp; q < a.nunits; q += (int64_t)gridDim.x * kNbWarps) {
+    const unsigned long long pool_cap = (unsigned long long)a.pool_cap;
+    for (int64_t q = (int64_t)blockIdx.x * kNbtWarps + warp; q < a.nunits; q += (int64_t)gridDim.x * kNbtWarps) {
         const WorkItem U = a.units[q];
         const PatchDev* P = a.pd + U.patch;
         const int64_t i = U.begin + lane;
         const bool act = i < U.end;
-        uint32_t cnt = 0, own = 0;
-        if (act) cnt = thread_walk<false>(a, P, i, S.rows + lane * kRowStride, false, 0, own);
-        const uint32_t v = act ? cnt : 0u;
-        uint32_t inc = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
+        // reservation: the hint plus a margin, or the counted length
+        uint32_t res = 0;
+        if (act) {
+            const uint32_t hint = a.rowcap[i];
+            if (hint == kNoHint) {
+                uint32_t own0 = 0;
+                res = round8(thread_walk<kWalkCount, K>(a, P, i, RowOut{nullptr, 0u, nullptr}, own0));
+            } else {
+                const uint32_t c = min(hint, (uint32_t)a.n);
+                res = round8(c + c / 3u + kHintMargin);
+            }
         }
+        const uint32_t inc = warp_incl_scan(res, lane);
         const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
         unsigned long long base = 0;
-        if (lane == 0) {
-            base = atomicAdd(a.pool_used, (unsigned long long)tot);
-            if (base + tot > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
-        }
+        if (lane == 0) base = atomicAdd(&a.pool_used[0], (unsigned long long)tot);
         base = __shfl_sync(0xffffffffu, base, 0);
-        const unsigned long long r0 = base + (inc - v);
-        const bool fits = base + tot <= (unsigned long long)a.max_pairs;
+        const bool ok = base + tot <= pool_cap;
+        if (!ok && lane == 0) atomicOr(a.status, kStOverflow);
+        unsigned long long r0 = base + (inc - res);
+        uint32_t cnt = 0, own = 0;
+        if (act) cnt = thread_walk<kWalkRing, K>(a, P, i, RowOut{a.col + r0, ok ? res : 0u, ring}, own);
+        if (act && ok && cnt > res) {
+            // outgrew the reservation: walk again into an exact one
+            const uint32_t need = round8(cnt);
+            r0 = atomicAdd(&a.pool_used[0], (unsigned long long)need);
+            if (r0 + need <= pool_cap) {
+                uint32_t own2 = 0;
+                thread_walk<kWalkDirect, K>(a, P, i, RowOut{a.col + r0, need, nullptr}, own2);
+            } else {
+                atomicOr(a.status, kStOverflow);
+            }
+        }
         if (act) {
             a.rowstart[i] = r0;
             a.cnt[i] = cnt;
             a.nown[i] = own;
         }
-        __syncwarp();
-        if (fits) {
-            const unsigned actm = __ballot_sync(0xffffffffu, act);
-            for (int l = 0; l < 32; l++) {
-                if (!((actm >> l) & 1u)) continue;
-                const uint32_t len = min(__shfl_sync(0xffffffffu, cnt, l), (uint32_t)kRowCap);
-                const unsigned long long rs = __shfl_sync(0xffffffffu, r0, l);
-                for (uint32_t k = lane; k < len; k += 32) a.col[rs + k] = S.rows[l * kRowStride + k];
-            }
-            const bool direct = act && cnt > (uint32_t)kRowCap;
-            if (direct) {
-                uint32_t own2 = 0;
-                thread_walk<true>(a, P, i, nullptr, true, r0, own2);
-            }
+        const uint32_t listed = __shfl_sync(0xffffffffu, warp_incl_scan(act ? cnt : 0u, lane), 31);
+        if (lane == 0) {
+            const unsigned long long before = atomicAdd(&a.pool_used[1], (unsigned long long)listed);
+            if (before + listed > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
         }
-        __syncwarp();
     }
 }
 
-int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp)
+template <int K>
+void launch_nb_thread(const Launch& L, const NbArgs& a)
+{
+    const size_t smem = sizeof(uint32_t) * 32 * kRing * kNbtWarps;
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_thread<K>, 32 * kNbtWarps, smem);
+        if (per_sm < 1) per_sm = 1;
+        // shared memory only for the rings of the resident CTAs: the rest is L1
+        int smem_max = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (smem_max > 0) {
+            const size_t need = (size_t)per_sm * (smem + 1024);
+            int pct = (int)((need * 100 + (size_t)smem_max - 1) / (size_t)smem_max);
+            pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+            cudaFuncSetAttribute(k_nb_thread<K>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        }
+    }
+    k_nb_thread<K><<<L.sms * per_sm, 32 * kNbtWarps, smem, L.stream>>>(a);
+}
+
+int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp, int K)
 {
     if (a.n <= 0 || a.nunits <= 0) return 0;
     if (tpp == 1) {
-        const size_t smem = sizeof(NbWarpSmem) * kNbWarps;
-        static bool attr1 = false;
-        if (!attr1) {
-            cudaFuncSetAttribute(k_nb_thread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr1 = true;
-        }
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_thread, 32 * kNbWarps, smem);
-        if (per_sm < 1) per_sm = 1;
-        k_nb_thread<<<L.sms * per_sm, 32 * kNbWarps, smem, L.stream>>>(a);
+        if (K == 1) launch_nb_thread<1>(L, a);
+        else launch_nb_thread<2>(L, a);
         return 1;
     }
     const size_t smem = sizeof(NbWarpSmem) * kNbWarps;

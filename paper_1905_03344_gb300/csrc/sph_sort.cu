@@ -481,8 +481,9 @@ int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, ui
 __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys, const uint32_t* svals,
                                                 State src, State dst, const uint32_t* perm_src,
                                                 uint32_t* perm_dst, const PatchDev* pd, Grid g,
-                                                Recs r, Fp64 f, int mixed)
+                                                Recs r, Fp64 f, int mixed, RowHint hint)
 {
+    const bool have_hint = *hint.valid != 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = skeys[k];
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
         dst.du_prev[k] = src.du_prev[si];
         dst.axp[k] = axp; dst.ayp[k] = ayp; dst.azp[k] = azp;
         perm_dst[k] = perm_src[si];
+        hint.rowcap[k] = have_hint ? hint.cnt_prev[si] : kNoHint;
 
         const uint32_t mort = key & ((1u << kPatchShift) - 1u);
         const uint32_t cx = compact1by2(mort), cy = compact1by2(mort >> 1), cz = compact1by2(mort >> 2);
@@ -529,11 +531,12 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
 
 int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint32_t* svals,
                   const State& src, const State& dst, const uint32_t* perm_src, uint32_t* perm_dst,
-                  const PatchDev* pd, const Grid& g, const Recs& r, const Fp64& f, int mixed)
+                  const PatchDev* pd, const Grid& g, const Recs& r, const Fp64& f, int mixed,
+                  const RowHint& hint)
 {
     if (n <= 0) return 0;
     k_gather<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, skeys, svals, src, dst, perm_src,
-                                                                 perm_dst, pd, g, r, f, mixed);
+                                                                 perm_dst, pd, g, r, f, mixed, hint);
     return 1;
 }
 

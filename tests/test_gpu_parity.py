@@ -173,6 +173,31 @@ def test_square_patch_ten_steps(B, orc, precision, tol, report):
     sim.close()
 
 
+def test_rows_outgrowing_their_reservation(B, orc, report):
+    """h grows fast (n_target far above the initial counts), so many rows
+    outgrow the space reserved from the previous step's row lengths and are
+    searched again into a second reservation; the trajectory must not notice."""
+    f = inputs.random_cloud(2000, seed=31, h_lo=0.07, h_hi=0.09, vscale=0.5)
+    n = len(f["x"])
+    kw = dict(n_target=150.0)
+    ref = orc.Sim(f, **kw)
+    counts = []
+    for step in range(3):
+        nb = orc.neighbors(ref["x"], ref["y"], ref["z"], ref["h"], 1.0)
+        counts.append(np.diff(nb.off).astype(np.int64))
+        ref.step(1)
+    # precondition, from the oracle alone: some rows exceed c + c/3 + 8
+    c0, c1 = counts[0], counts[1]
+    assert np.sum(c1 > ((c0 + c0 // 3 + 8 + 7) // 8) * 8) > n // 20
+    sim = B.SPH(n, precision="fp64", max_pairs=cap_pairs(n), **kw)
+    sim.set_particles(f)
+    sim.step(3)
+    g = {k: sim.field(k) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "nown", "rho", "ax", "ay", "az")}
+    sim.close()
+    assert np.array_equal(g["nown"], ref["nown"])
+    report["outgrow/fp64"] = _compare_state(g, ref, 1e-11, "outgrow")
+
+
 def test_batched_patches_match_single(B, orc):
     rng = np.random.default_rng(3)
     edges = [6, 9, 7, 11]
