@@ -32,9 +32,22 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # FP32 operations per pair (FMA = 2, MUFU not counted), counted by hand from
-# k_momentum_mixed and k_density_mixed (see the per-line count in the design doc)
+# k_momentum_mixed and k_density_mixed (the per-line count is in the design notes)
 FLOPS_PER_PAIR_MOMENTUM = 80
 FLOPS_PER_PAIR_DENSITY = 28
+# Algorithmic bytes of the neighbour-list kernel (k_nb_thread): 4 B per list
+# entry written, and per particle the row start (8 B), length (4 B) and own
+# count (4 B) written plus its record (16 B), h (8 B), cell (4 B) and row hint
+# (4 B) read once.
+NB_BYTES_PER_ENTRY = 4
+NB_BYTES_PER_PARTICLE = 48
+# DRAM bytes (read + write) per list entry of one launch, from ncu captures
+# of the 100^3 patch (dram__bytes_read.sum + dram__bytes_write.sum divided by
+# the launch's list entries; profiles/k_nb_thread_square_patch_100cubed.md and
+# profiles/k_momentum_mixed_square_patch_100cubed.md), scaled to the
+# benchmark's launch by its entries.  None once the kernel has changed.
+NB_DRAM_BYTES_PER_ENTRY = 4.49
+MOMENTUM_DRAM_BYTES_PER_ENTRY = 5.78
 
 WORKLOADS = {
     "c1": ("square patch 20^3 (8,000 particles), omega=5", 20),
@@ -174,7 +187,6 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--graph", action="store_true", help="replay the step as a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -204,7 +216,11 @@ def main():
         sim.set_particles(dfields)
         return sim
 
-    sim = make(args.precision, args.graph)
+    # FP32 FMA rate of this GPU (0.3 s, before anything is timed)
+    fma_peak = binding.sph_fma_peak("fp64" if args.precision == "fp64" else "mixed",
+                                    stream=stream.cuda_stream) / 1e12
+
+    sim = make(args.precision, True)
     for _ in range(args.warmup):
         sim.step(1)
     if not args.no_autotune:
@@ -214,9 +230,10 @@ def main():
     tpp, cf = binding.sph_get_tuning(sim.ctx)
     torch.cuda.synchronize()
     sim.pair_count(reset=True)
-    if not args.graph:
-        sim.profile(True)
-        sim.profile()      # reset accumulators
+    # the timed region runs the phases with CUDA events between them (per-kernel
+    # durations for the roofline); the graph is bypassed while profiling
+    sim.profile(True)
+    sim.profile()      # reset accumulators
     clocks = Clocks(local)
     l0 = sim.launches()
     if world > 1:
@@ -236,7 +253,23 @@ def main():
     ms_total = e0.elapsed_time(e1)
     launches = sim.launches() - l0
     pairs = sim.pair_count(reset=True)
-    prof = sim.profile() if not args.graph else {}
+    prof = sim.profile()
+    sim.profile(False)
+
+    # the same steps replayed from the captured CUDA graph (one graph per
+    # buffer parity, captured during the two untimed steps)
+    for _ in range(2):
+        sim.step(1)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1)
+    pairs_graph = sim.pair_count(reset=True)
     if world > 1:
         t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -251,21 +284,33 @@ def main():
     steps_per_s = args.steps / sec
     pairs_per_step = pairs / args.steps
 
-    # dominant kernel: momentum/energy pair sum (FP32 pipe)
     peaks, peak_src = measured_peaks()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * (peaks.get("sm_max_mhz") or SM_MAX_MHZ) * 1e6 / 1e12
-    roof = None
-    if prof:
-        mom_ms = prof["momentum"][0] / max(args.steps, 1)
-        achieved = FLOPS_PER_PAIR_MOMENTUM * pairs_per_step / (mom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_momentum_mixed" if args.precision == "mixed" else "k_momentum_fp64",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": None,
+    sm_max = peaks.get("sm_max_mhz") or SM_MAX_MHZ
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # dominant kernel: the neighbour-list search (k_nb_thread), HBM roofline
+    # on its algorithmic bytes
+    nb_ms = prof["nb"][0] / max(args.steps, 1)
+    nb_bytes = NB_BYTES_PER_ENTRY * pairs_per_step + NB_BYTES_PER_PARTICLE * n
+    nb_gbs = nb_bytes / (nb_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_nb_thread", "achieved": nb_gbs, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": nb_gbs / peaks["hbm_gbs"],
+            "traffic": (NB_DRAM_BYTES_PER_ENTRY * pairs_per_step) if NB_DRAM_BYTES_PER_ENTRY else None,
+            "algorithmic_bytes": nb_bytes, "ms_per_launch": nb_ms,
+            "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src,
+            "share_of_step": prof["nb"][0] / ms_total}
+    # the pair sums: FP32 pipe (mixed) against the derived FP32 peak
+    mom_ms = prof["momentum"][0] / max(args.steps, 1)
+    mom_tf = FLOPS_PER_PAIR_MOMENTUM * pairs_per_step / (mom_ms / 1e3) / 1e12
+    roof_mom = {"bound": "alu", "kernel": "k_momentum_mixed" if args.precision == "mixed" else "k_momentum_fp64",
+                "achieved": mom_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak,
+                "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step) if MOMENTUM_DRAM_BYTES_PER_ENTRY else None,
                 "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
-                               % (SMS, FP32_LANES_PER_SM, peaks.get("sm_max_mhz") or SM_MAX_MHZ),
-                "flops_per_pair": FLOPS_PER_PAIR_MOMENTUM, "ms_per_launch": mom_ms}
-        if clk.get("sm_mhz"):
-            roof["frac_at_sampled_clock"] = achieved / (fp32_peak * clk["sm_mhz"] / (peaks.get("sm_max_mhz") or SM_MAX_MHZ))
+                               % (SMS, FP32_LANES_PER_SM, sm_max),
+                "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf / fma_peak,
+                "flops_per_pair": FLOPS_PER_PAIR_MOMENTUM, "ms_per_launch": mom_ms,
+                "share_of_step": prof["momentum"][0] / ms_total}
+    if clk.get("sm_mhz"):
+        roof_mom["frac_at_sampled_clock"] = mom_tf / (fp32_peak * clk["sm_mhz"] / sm_max)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -278,14 +323,16 @@ def main():
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
-                   "threads_per_particle": tpp, "cell_factor": cf, "graph": bool(args.graph)},
+                   "threads_per_particle": tpp, "cell_factor": cf,
+                   "timed": "K steps with CUDA events between phases (no graph)"},
         "steps_per_s": steps_per_s, "pairs_per_step": pairs_per_step,
         "gpu_launches": launches, "clocks": clk,
+        "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "roofline": roof, "roofline_pair_sum": roof_mom,
+        "graph_replay": {"value": 2.0 * pairs_graph / (ms_graph / 1e3), "unit": UNIT,
+                         "ms_per_step": ms_graph / args.steps, "steps_per_s": 1e3 * args.steps / ms_graph,
+                         "steps": args.steps},
     }
-    if prof:
-        line["phase_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
-    if roof:
-        line["roofline"] = roof
 
     # FP64 GPU path on the same patch
     if args.fp64_steps > 0 and args.precision == "mixed":

@@ -252,6 +252,18 @@ sph_status sph_conserved_noalloc(int64_t n, const double* x, const double* y, co
                                  const double* u, double* out, void* cuda_stream);
 const char* sph_noalloc_last_error(void);
 
+/* The fused multiply-add rate of this GPU in FLOP/s (an FMA counts 2): a
+ * kernel of independent FMA chains on every SM, 8 CTAs of 256 threads per SM,
+ * timed with CUDA events over runs of at least 50 ms, best of three.
+ * precision: SPH_MIXED measures FP32 FMA, SPH_FP64 measures FP64 FMA.  It is
+ * the roofline denominator of the pair sums, which are bound by those pipes.
+ * The paper has no counterpart.  Synchronous on cuda_stream (a cudaStream_t
+ * or NULL); runs for about 0.3 s on the current device; allocates nothing
+ * but two events.  Errors: SPH_EINVAL, SPH_ECUDA;
+ * sph_fma_peak_last_error() gives the message. */
+sph_status sph_fma_peak(int32_t precision, double* flop_per_s, void* cuda_stream);
+const char* sph_fma_peak_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,8 @@ SIGNATURES = {
     "sph_get_pair_count": (_ST, [_P, ctypes.POINTER(_I64), ctypes.c_int]),
     "sph_conserved_noalloc": (_ST, [_I64] + [_P] * 8 + [_P]),
     "sph_noalloc_last_error": (ctypes.c_char_p, []),
+    "sph_fma_peak": (_ST, [_I32, _P, _P]),
+    "sph_fma_peak_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -313,6 +315,17 @@ def sph_conserved_noalloc(fields, out, stream=None):
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
     if st != SPH_OK:
         raise SphError(st, lib().sph_noalloc_last_error().decode())
+
+
+def sph_fma_peak(precision="mixed", stream=None):
+    """FP32 (precision "mixed") or FP64 ("fp64") fused multiply-add rate of the
+    current device in FLOP/s, measured by the library's FMA-chain kernel."""
+    v = ctypes.c_double()
+    st = lib().sph_fma_peak(SPH_FP64 if precision == "fp64" else SPH_MIXED, ctypes.byref(v),
+                            ctypes.c_void_p(stream or 0))
+    if st != SPH_OK:
+        raise SphError(st, lib().sph_fma_peak_last_error().decode())
+    return v.value
 
 
 # ---- object wrapper -----------------------------------------------------------

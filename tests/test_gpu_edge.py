@@ -198,3 +198,14 @@ def test_profile_and_launch_counts(B):
     assert prof["momentum"][1] == 2 and prof["density"][1] == 2
     assert sim.pair_count() > 0
     sim.close()
+
+
+@pytest.mark.gpu
+def test_fma_peak_plausible(B):
+    """The FMA-chain rate: FP32 at least a few tens of TFLOP/s on a GB300 and
+    FP64 far below it (the reduced FP64 pipe); a rate above the SM count x
+    lanes x 2 x 3 GHz would mean the chains were optimised away."""
+    f32 = B.sph_fma_peak("mixed")
+    f64 = B.sph_fma_peak("fp64")
+    assert 10e12 < f32 < 152 * 128 * 2 * 3.0e9
+    assert 0.05e12 < f64 < f32 / 4
