@@ -126,17 +126,20 @@ sph_status sph_set_particles(sph_ctx* ctx, int64_t n, const double* x, const dou
  * Errors: SPH_EINVAL, SPH_ESTATE. */
 sph_status sph_set_patches(sph_ctx* ctx, int32_t n_patches, const int64_t* offsets);
 
-/* Neighbour discovery (Table 1): per patch bounding box and Morton keys,
- * radix sort into cells, cell ranges, neighbour counts, exclusive scan and
- * CSR fill.  j is a neighbour of i iff j != i and r_ij^2 < 4 h_i^2 or
- * r_ij^2 < 4 h_j^2 (minimum image along z), decided exactly in FP64.
+/* Neighbour discovery (Table 1): per patch bounding box, h histogram and
+ * class threshold, Morton keys, radix sort into cells, cell ranges, and one
+ * search per particle that writes its row into the list pool.  j is a
+ * neighbour of i iff j != i and r_ij^2 < 4 h_i^2 or r_ij^2 < 4 h_j^2
+ * (minimum image along z), decided exactly in FP64.
  * Errors: SPH_EOVERFLOW (more than max_pairs entries), SPH_ESTATE. */
 sph_status sph_find_neighbors(sph_ctx* ctx);
 
 /* Borrowed device pointers to the last neighbour lists as a canonical CSR in
  * sorted order: row k (sorted particle k) holds col[off[k] .. off[k+1]) as
  * sorted indices; perm[k] is the original index of sorted particle k.  Within
- * a row, columns are grouped by cell, ascending inside each cell.  (The
+ * a row, the neighbours with h below the patch's class threshold come first,
+ * grouped by cell and ascending inside each cell, then the few above it
+ * (grouped by coarse cell, ascending inside each).  (The
  * timestep itself reads the rows where the search wrote them -- contiguous
  * rows with a start and a length each; this call lays them out with prefix
  * offsets.)  Any output pointer may be NULL. */

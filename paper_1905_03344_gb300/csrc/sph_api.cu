@@ -70,7 +70,7 @@ struct sph_ctx {
     int cap_patch = 0, cap_items = 0;
     int64_t n = 0;
     int npatch = 0, nitems = 0, radix_passes = 3;
-    int tpp_nb = 1, tpp_pair = 8;
+    int tpp_pair = 8;
     double cell_factor = 0.5;
     int mixed = 1;
 
@@ -254,6 +254,7 @@ PairArgs pair_args(sph_ctx* ctx)
     a.rowstart = ctx->rowstart;
     a.cnt = ctx->cnt;
     a.col = ctx->col;
+    a.cellxyz = ctx->grid.cellxyz;
     a.s = ctx->st[ctx->cur];
     a.r = ctx->rec;
     a.f = ctx->f64;
@@ -298,6 +299,7 @@ void enqueue_sort(sph_ctx* ctx)
         Phase p(ctx, SPH_PHASE_BBOX);
         ctx->launches += launch_reset_red(L, ctx->npatch, ctx->red);
         ctx->launches += launch_reduce_bbox(L, ctx->st[ctx->cur], ctx->items, ctx->nitems, ctx->red);
+        ctx->launches += launch_h_hist(L, ctx->st[ctx->cur], ctx->items, ctx->nitems, ctx->red);
         ctx->launches += launch_grid_params(L, ctx->npatch, ctx->red, ctx->pd, ctx->cell_factor, ctx->status);
     }
     {
@@ -333,7 +335,7 @@ void enqueue_lists(sph_ctx* ctx)
     ctx->canon_valid = false;
     {
         Phase p(ctx, SPH_PHASE_NB);
-        ctx->launches += launch_nb_lists(L, a, ctx->tpp_nb, ctx->cell_factor >= 1.0 ? 1 : 2);
+        ctx->launches += launch_nb_lists(L, a, ctx->cell_factor >= 1.0 ? 1 : 2);
     }
     // the row lengths now belong to the current order: hints for the next sort
     cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
@@ -417,7 +419,7 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
         P.end = offsets[p + 1];
         const int64_t np_ = P.end - P.begin;
         int64_t cap = 2 * np_ + 4096;
-        const int64_t maxc = (int64_t)kMaxCellsAxis * kMaxCellsAxis * kMaxCellsAxis;
+        const int64_t maxc = (int64_t)kMaxCellsAxis * kMaxCellsAxis * kMaxCellsAxis * 9 / 8 + 64;
         if (cap > maxc) cap = maxc;
         P.cell_base = cbase;
         P.cell_cap = cap;
@@ -597,7 +599,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     }
     ctx->mixed = cfg.precision == SPH_MIXED;
     ctx->cell_factor = cfg.cell_factor;
-    if (t) ctx->tpp_nb = ctx->tpp_pair = t;
+    if (t) ctx->tpp_pair = t;
     ctx->cap_n = cfg.max_particles;
     ctx->cap_patch = cfg.max_patches;
     ctx->max_pairs = cfg.max_pairs > 0 ? cfg.max_pairs : 160 * cfg.max_particles;
@@ -1064,7 +1066,6 @@ sph_status sph_autotune(sph_ctx* ctx)
     ctx->prof = false;
     destroy_graphs(ctx);
     const double factors[3] = {0.5, 0.75, 1.0};
-    const int nb_tpps[2] = {1, 32};
     const int pair_tpps[4] = {4, 8, 16, 32};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1083,19 +1084,13 @@ sph_status sph_autotune(sph_ctx* ctx)
         return best;
     };
     double best_total = 1e300, best_f = ctx->cell_factor;
-    int best_nb = ctx->tpp_nb, best_pair = ctx->tpp_pair;
+    int best_pair = ctx->tpp_pair;
     for (double f : factors) {
         ctx->cell_factor = f;
         enqueue_sort(ctx);
-        float bnb = 1e30f, bpair = 1e30f;
-        int tnb = 1, tpair = 8;
-        for (int t : nb_tpps) {
-            ctx->tpp_nb = t;
-            float ms = timeit([&] { enqueue_lists(ctx); });
-            if (ms < bnb) { bnb = ms; tnb = t; }
-        }
-        ctx->tpp_nb = tnb;
-        enqueue_lists(ctx);
+        float bpair = 1e30f;
+        int tpair = 8;
+        const float bnb = timeit([&] { enqueue_lists(ctx); });
         for (int t : pair_tpps) {
             ctx->tpp_pair = t;
             float ms = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
@@ -1105,14 +1100,12 @@ sph_status sph_autotune(sph_ctx* ctx)
         if (tot < best_total) {
             best_total = tot;
             best_f = f;
-            best_nb = tnb;
             best_pair = tpair;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->cell_factor = best_f;
-    ctx->tpp_nb = best_nb;
     ctx->tpp_pair = best_pair;
     ctx->prof = prof0;
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;

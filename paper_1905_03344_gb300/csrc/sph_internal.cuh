@@ -1,11 +1,16 @@
 // sph_internal.cuh -- device data layout and launch declarations shared by
 // the CUDA translation units of libsph_gb300.so.  Not part of the C ABI.
 //
-// Particles live in HBM as structure-of-arrays, sorted by (patch, Morton
-// cell).  Per patch, a uniform grid of cells with edge s >= 2 h_max *
-// cell_factor covers the bounding box in x, y and the period lz in z; a
-// particle searches the (2K+1)^3 cells around its own (K = 1 for
-// cell_factor >= 1, K = 2 below), pruned by each cell's largest h.
+// Particles live in HBM as structure-of-arrays, sorted by (patch, class,
+// Morton cell).  Per patch, the particles with h <= h_s are "small" and the
+// few above are "big" (h_s: a high quantile of h, so that about 1/64 of the
+// patch is big).  A uniform grid of cells with edge s >= 2 h_s cell_factor
+// covers the bounding box in x, y and the period lz in z; a small particle
+// searches the (2K+1)^3 cells around its own (K = 1 for cell_factor >= 1,
+// K = 2 below) for small neighbours, pruned by each cell's largest h.  Big
+// particles are indexed separately by coarse cells (aligned blocks of 2^kc
+// fine cells with edge >= 2 h_max), which every particle searches for big
+// neighbours; a big particle searches the fine grid as far as its own 2 h.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,15 +21,19 @@
 
 namespace sphg {
 
-constexpr int kMortonBits = 8;                 // per axis: at most 256 cells
+constexpr int kMortonBits = 7;                 // per axis: at most 128 cells
 constexpr int kMaxCellsAxis = 1 << kMortonBits;
-constexpr int kPatchShift = 3 * kMortonBits;   // key = patch << 24 | morton
+constexpr int kClassShift = 3 * kMortonBits;   // key = patch << 22 | big << 21 | morton
+constexpr int kPatchShift = kClassShift + 1;
+constexpr uint32_t kMortonMask = (1u << kClassShift) - 1u;
 constexpr int kColBits = 25;                   // packed column: j | stencil << 25
 constexpr uint32_t kColMask = (1u << kColBits) - 1u;
 constexpr int64_t kMaxParticles = int64_t(1) << kColBits;
 constexpr int kMaxPatches = 256;
 constexpr int kItemChunk = 4096;               // particles per work item
 constexpr int kStencilCells = 125;             // (2K+1)^3 for K <= 2
+constexpr uint32_t kFarCode = 127;             // column stencil code: offset from the cell coordinates
+constexpr int kBigShare = 64;                  // about 1/kBigShare of a patch is big
 
 // status word bits (device, sticky until the host clears it)
 constexpr int kStOverflow = 1;
@@ -52,15 +61,23 @@ struct PatchDev {
     float s_f, sz_f, lz_f, inv_s_f, inv_sz_f, hmax_f;
     int32_t ncx, ncy, ncz, K;
     int32_t zmode;               // 0: 2K+1 distinct z cells; 1: all z cells + float wrap
-    int32_t pad;
+    int32_t nbig;                // big particles (h > hs), counted by the key kernel
+    double hs;                   // class threshold: small iff h <= hs
+    float hs_f;
+    int32_t kc;                  // coarse cell = 2^kc fine cells per axis
+    int32_t ncxc, ncyc, nczc;    // coarse grid
+    int32_t zmode_c;             // 0: 3 distinct coarse z cells; 1: all of them
+    int64_t coarse_base;         // first coarse cell in the cell tables
     // time state
     double dt, dt_prev;
     int64_t step;
 };
 
 // Per-patch reduction slots, ordered-integer encoded doubles.
+constexpr int kHBins = 64;       // histogram of h / h_max for the class threshold
 struct PatchRed {
     unsigned long long xmin, ymin, xmax, ymax, hmax, hcmin;
+    uint32_t hist[kHBins];
 };
 
 struct WorkItem {
@@ -74,7 +91,8 @@ struct State {
 };
 
 struct Grid {
-    uint2* cse;          // [cell] (start, end) in sorted order, 0/0 = empty
+    uint2* cse;          // [cell] (start, end) in sorted order, 0/0 = empty; fine
+                         // cells hold small particles, coarse cells big ones
     float* chmax;        // [cell] largest h (FP32) in the cell
     uint32_t* cellxyz;   // [particle] cx | cy << 8 | cz << 16
     const uint16_t* patch_of;  // [particle] patch index
@@ -141,10 +159,11 @@ struct Launch {
 
 int launch_reduce_bbox(const Launch& L, const State& s, const WorkItem* items, int nitems,
                        PatchRed* red);
+int launch_h_hist(const Launch& L, const State& s, const WorkItem* items, int nitems, PatchRed* red);
 int launch_grid_params(const Launch& L, int npatch, const PatchRed* red, PatchDev* pd,
                        double cell_factor, int* status);
 int launch_keys(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of,
-                const PatchDev* pd, uint32_t* keys, uint32_t* vals);
+                PatchDev* pd, uint32_t* keys, uint32_t* vals);
 // LSD radix sort of (keys, vals); result in (keys, vals); uses alternates.
 int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, uint32_t* vals,
                       uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist, uint32_t* scan_tmp);
@@ -184,7 +203,7 @@ struct NbArgs {
     int* status;
 };
 // K: stencil half-extent of every patch (1 for cell_factor >= 1, else 2)
-int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp, int K);
+int launch_nb_lists(const Launch& L, const NbArgs& a, int K);
 int launch_canonical_rows(const Launch& L, int64_t n, const unsigned long long* rowstart,
                           const uint32_t* cnt, const uint64_t* off, const uint32_t* col, uint32_t* out);
 // exclusive scan of n u32 values into u64 out[0..n], out[n] = total
@@ -197,6 +216,7 @@ struct PairArgs {
     const unsigned long long* rowstart;  // row i is col[rowstart[i] .. + cnt[i])
     const uint32_t* cnt;
     const uint32_t* col;
+    const uint32_t* cellxyz;             // [particle] cell, for kFarCode columns
     State s;
     Recs r;
     Fp64 f;

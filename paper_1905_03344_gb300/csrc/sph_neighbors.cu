@@ -4,53 +4,43 @@
 // minimum image along periodic z.  n_i = #{j : r_ij^2 < 4 h_i^2} feeds the
 // smoothing-length adaptation.
 //
-// One warp serves 32 consecutive sorted particles of one patch, one lane per
-// particle.  The warp expresses its particles in the frame of a reference
-// cell, takes their bounding box, and enumerates the block of cells around
-// it, keeping the non-empty cells closer than 2 max(h_warp, h_max(cell)).
-// The candidates of the kept cells are staged 32 at a time in shared memory
-// (shifted into the reference frame) and every lane tests all 32 against its
-// own particle, so each candidate is loaded once per warp and the inner loop
-// is a shared-memory broadcast plus FP32 arithmetic.  A candidate is decided
-// in FP32 only outside a guard band around the threshold; inside it the FP64
-// predicate is evaluated with the same operation order and rounding as its
-// definition, so the lists are bit-exact.  Lanes farther than kSpanMax cells
-// from the reference cell are served in a later pass of the same warp.
+// One thread per particle; a warp serves 32 consecutive sorted particles of
+// one patch.  The search has up to three parts, each visiting every
+// candidate of its kind once:
+//   small i, small j: the (2K+1)^3 fine cells around i's cell (template K),
+//     pruned by distance against 2 max(h_i, h_max(cell));
+//   big i, small j:   the fine cells within 2 h_i of i (runtime extent);
+//   any i, big j:     the 3 x 3 x 3 coarse cells around i's coarse cell
+//     (only when the patch has big particles).
+// Small particles never reach farther than 2 h_s, and every big one lies in
+// the coarse block of any particle it can reach, so the parts together find
+// every neighbour exactly once.  A candidate is decided in FP32 only outside
+// a guard band around the threshold; inside it the FP64 predicate is
+// evaluated with the same operation order and rounding as its definition, so
+// the lists are bit-exact.
 //
-// Each lane stages its row in shared memory (ordered by position in the cell
-// block, then by sorted index); the warp then reserves the rows of the pass
-// in the list pool with one atomic add and writes them with coalesced
-// stores.  Rows longer than the staging slot are written straight to the
-// pool by a second walk over the same candidates.  Row contents are fixed by
-// the inputs; only the place of a warp's rows in the pool depends on
-// scheduling, and every consumer reads a row through its start and length,
-// so all results are bitwise reproducible.  The canonical CSR with prefix
-// offsets is built from the pool on demand (sph_get_neighbors).  Nothing
-// waits on another warp.
+// Rows go straight to the pool.  Each lane reserves its row before the walk,
+// from the row-length hint c (the particle's row length in the previous
+// lists) as c + c/3 + 8 entries -- on a lattice a small change of h adds a
+// whole shell of neighbours at once, up to about a third of the row -- or,
+// without a hint, from a first walk that only counts.  Reservations are
+// rounded up to a multiple of 8 entries, so every row starts on a 32-byte
+// boundary.  Hits collect in a 16-slot ring in shared memory and leave it as
+// whole 32-byte sectors.  A row that outgrows its reservation is walked again
+// into a fresh reservation of its exact (rounded) length.  Shared memory per
+// warp is 2 KB, which leaves the SM's L1 to the candidate gathers.  Row
+// contents are fixed by the inputs; only the place of a row in the pool
+// depends on scheduling, and every consumer reads a row through its start
+// and length, so all results are bitwise reproducible.  The canonical CSR
+// with prefix offsets is built from the pool on demand (sph_get_neighbors).
+//
+// Column word: j | code << 25, code = (dcx+2) + 5 (dcy+2) + 25 zd for a
+// neighbour within two fine cells (zd = dcz + 2 with distinct z cells, the z
+// cell count offset when all z cells are visited), kFarCode otherwise (the
+// pair sums then take the offset from both particles' cell coordinates).
 #include "sph_internal.cuh"
 
 namespace sphg {
-
-constexpr int kNbWarps = 2;            // warps per CTA
-constexpr int kRowCap = 128;           // staged entries per lane
-constexpr int kRowStride = kRowCap + 1;
-constexpr int kKeptMax = 64;           // kept-cell batch
-constexpr int kSpanMax = 2;            // cells between a lane and the reference cell
-
-struct NbWarpSmem {
-    uint32_t rows[32 * kRowStride];    // staged rows, one per lane
-    float4 tq[32];                     // candidate tile: position in the reference frame, 4 h^2
-    uint32_t tj[32];                   // candidate index
-    uint32_t tb[32];                   // candidate cell, packed offset from the reference cell
-    uint32_t kst[kKeptMax];            // kept cells: first particle
-    uint32_t kpre[kKeptMax];           // kept cells: prefix of the lengths
-    uint32_t kb[kKeptMax];             // kept cells: packed offset from the reference cell
-};
-
-__device__ __forceinline__ uint32_t pack3(int bx, int by, int bz)
-{
-    return (uint32_t)(bx + 128) | ((uint32_t)(by + 128) << 8) | ((uint32_t)(bz + 128) << 16);
-}
 
 // exact FP64 predicate, no contraction: bit 0 union, bit 1 own radius
 __device__ __forceinline__ int exact_pair(double xi, double yi, double zi, double hi, double xj,
@@ -75,315 +65,6 @@ __device__ __noinline__ int exact_pair_at(const NbArgs& a, int64_t i, uint32_t j
     return exact_pair(a.x[i], a.y[i], a.z[i], a.h[i], a.x[j], a.y[j], a.z[j], a.h[j], lz);
 }
 
-__device__ __forceinline__ float warp_min(float v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// gap between [lo, hi] and the cell [b s, (b+1) s) along one axis
-__device__ __forceinline__ float box_gap(float lo, float hi, int b, float s)
-{
-    const float c0 = (float)b * s, c1 = c0 + s;
-    return fmaxf(fmaxf(c0 - hi, lo - c1), 0.0f);
-}
-
-struct LaneState {
-    float ox, oy, oz;      // particle in the reference frame
-    float Ti, flo, fhi;    // 4 h_i^2 and the guard band
-    int dx, dy, dz;        // cell offset from the reference cell
-    uint32_t kki;          // (dx + 5 dy + 25 dz) << kColBits
-    uint32_t cnt, own;
-    int64_t i;
-    bool act;              // lane takes part in this pass
-};
-
-struct WarpBox {
-    int refx, refy, refz;
-    float x0, y0, z0, x1, y1, z1;  // bounding box of the pass, reference frame
-    float hw;                      // largest h of the pass
-};
-
-// One walk over the candidates of the lanes in L.act.  DIRECT = false: rows
-// are staged in shared memory (up to kRowCap entries); DIRECT = true: lanes
-// with direct = true write their whole row to the pool at r0.
-template <bool DIRECT>
-__device__ void warp_walk(const NbArgs& a, const PatchDev* P, NbWarpSmem& S, LaneState& L, int lane,
-                          const WarpBox& B, bool direct, unsigned long long r0)
-{
-    const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
-    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz, zmode = P->zmode;
-    const uint32_t cbase = (uint32_t)P->cell_base;
-    const float slack = (1.0f / 4096.0f) * s_f;
-    const float Rmax = 2.0f * fmaxf(B.hw, P->hmax_f) * (1.0f + 1.0f / 512.0f) + slack;
-    // block of cells around the bounding box, as offsets from the reference cell
-    const int xlo = max((int)floorf((B.x0 - Rmax) / s_f), -B.refx);
-    const int xhi = min((int)floorf((B.x1 + Rmax) / s_f), ncx - 1 - B.refx);
-    const int ylo = max((int)floorf((B.y0 - Rmax) / s_f), -B.refy);
-    const int yhi = min((int)floorf((B.y1 + Rmax) / s_f), ncy - 1 - B.refy);
-    const int zlo = (int)floorf((B.z0 - Rmax) / sz_f);
-    int zhi = (int)floorf((B.z1 + Rmax) / sz_f);
-    // a block longer than the period would visit a z cell twice: take one
-    // full period instead and the minimum image in FP32
-    const bool zwrap = zmode != 0 || (zhi - zlo + 1) >= ncz;
-    if (zwrap) zhi = zlo + ncz - 1;
-    const int nbx = xhi - xlo + 1, nby = yhi - ylo + 1, nbz = zhi - zlo + 1;
-    const int nbox = (nbx > 0 && nby > 0) ? nbx * nby * nbz : 0;
-    const unsigned ltmask = (1u << lane) - 1u;
-    uint32_t nk = 0, ktot = 0;
-
-    auto flush = [&]() {
-        // candidates of the kept batch, 32 per tile
-        for (uint32_t fb = 0; fb < ktot; fb += 32) {
-            const uint32_t f = fb + lane;
-            if (f < ktot) {
-                uint32_t c = 0;
-                while (c + 1 < nk && S.kpre[c + 1] <= f) c++;
-                const uint32_t j = S.kst[c] + (f - S.kpre[c]);
-                const uint32_t pb = S.kb[c];
-                const float4 q = a.r4[j];
-                const int bx = (int)(pb & 255u) - 128, by = (int)((pb >> 8) & 255u) - 128,
-                          bz = (int)((pb >> 16) & 255u) - 128;
-                S.tq[lane] = make_float4(fmaf((float)bx, s_f, q.x), fmaf((float)by, s_f, q.y),
-                                         fmaf((float)bz, sz_f, q.z), q.w);
-                // column word for a particle of the reference cell; a lane d cells
-                // away subtracts d from the stencil code (exact when |offset| <= 2)
-                S.tj[lane] = j | ((uint32_t)((bx + 2) + 5 * (by + 2) + 25 * (bz + 2)) << kColBits);
-                S.tb[lane] = pb;
-            }
-            __syncwarp();
-            const uint32_t nt = min(32u, ktot - fb);
-            if (L.act) {
-                for (uint32_t t = 0; t < nt; t++) {
-                    const float4 Q = S.tq[t];
-                    const float ex = L.ox - Q.x, ey = L.oy - Q.y;
-                    float ez = L.oz - Q.z;
-                    // the block may start a whole period away: nearest image
-                    if (zwrap) ez = fmaf(-lz_f, rintf(ez * inv_lz), ez);
-                    const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    const float T = fmaxf(L.Ti, Q.w);
-                    if (r2 > T * L.fhi) continue;
-                    const uint32_t tw = S.tj[t];
-                    const uint32_t j = tw & kColMask;
-                    if ((int64_t)j == L.i) continue;
-                    bool in = r2 < T * L.flo;
-                    bool io = r2 < L.Ti * L.flo;
-                    if (!in || (!io && r2 <= L.Ti * L.fhi)) {
-                        const int e = exact_pair(a.x[L.i], a.y[L.i], a.z[L.i], a.h[L.i], a.x[j], a.y[j], a.z[j],
-                                                 a.h[j], P->lz);
-                        in = e & 1;
-                        io = (e >> 1) & 1;
-                    }
-                    L.own += io;
-                    if (!in) continue;
-                    uint32_t w;
-                    if (!zwrap) {
-                        w = tw - L.kki;
-                    } else {
-                        // stencil code of j's cell relative to i's cell, periodic z
-                        const uint32_t pb = S.tb[t];
-                        const int dcx = (int)(pb & 255u) - 128 - L.dx;
-                        const int dcy = (int)((pb >> 8) & 255u) - 128 - L.dy;
-                        int dcz = (int)((pb >> 16) & 255u) - 128 - L.dz;
-                        int zd;
-                        if (zmode == 0) {
-                            dcz = ((dcz % ncz) + ncz) % ncz;
-                            if (dcz > ncz / 2) dcz -= ncz;
-                            zd = dcz + 2;
-                        } else {
-                            zd = ((dcz % ncz) + ncz) % ncz;
-                        }
-                        w = j | ((uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd) << kColBits);
-                    }
-                    if (DIRECT) {
-                        if (direct && r0 + L.cnt < (unsigned long long)a.pool_cap) a.col[r0 + L.cnt] = w;
-                    } else if (L.cnt < (uint32_t)kRowCap) {
-                        S.rows[lane * kRowStride + L.cnt] = w;
-                    }
-                    L.cnt++;
-                }
-            }
-            __syncwarp();
-        }
-        nk = 0;
-        ktot = 0;
-    };
-
-    for (int cb = 0; cb < nbox; cb += 32) {
-        const int c = cb + lane;
-        bool keep = false;
-        uint32_t st = 0, len = 0, pb = 0;
-        if (c < nbox) {
-            const int bx = xlo + c % nbx, by = ylo + (c / nbx) % nby, bz = zlo + c / (nbx * nby);
-            const int cxj = B.refx + bx, cyj = B.refy + by;
-            int czj = (B.refz + bz) % ncz;
-            if (czj < 0) czj += ncz;
-            const float gz = zwrap ? 0.0f : box_gap(B.z0, B.z1, bz, sz_f);
-            const float gx = box_gap(B.x0, B.x1, bx, s_f), gy = box_gap(B.y0, B.y1, by, s_f);
-            const float d2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-            if (d2 < Rmax * Rmax) {
-                const uint32_t lin =
-                    cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cxj;
-                const uint2 se = a.g.cse[lin];
-                if (se.x < se.y) {
-                    const float R = 2.0f * fmaxf(B.hw, a.g.chmax[lin]) * (1.0f + 1.0f / 512.0f) + slack;
-                    if (d2 < R * R) {
-                        keep = true;
-                        st = se.x;
-                        len = se.y - se.x;
-                        pb = pack3(bx, by, bz);
-                    }
-                }
-            }
-        }
-        uint32_t inc = len;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const uint32_t k = nk + (uint32_t)__popc(b & ltmask);
-            S.kst[k] = st;
-            S.kpre[k] = ktot + inc - len;
-            S.kb[k] = pb;
-        }
-        nk += (uint32_t)__popc(b);
-        ktot += __shfl_sync(0xffffffffu, inc, 31);
-        __syncwarp();
-        if (nk > (uint32_t)(kKeptMax - 32) || cb + 32 >= nbox) flush();
-    }
-}
-
-__global__ void __launch_bounds__(32 * kNbWarps) k_nb_warp(NbArgs a)
-{
-    extern __shared__ __align__(16) unsigned char nb_smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    NbWarpSmem& S = ((NbWarpSmem*)nb_smem)[warp];
-    if (*a.status & kStBad) return;
-    for (int64_t q = (int64_t)blockIdx.x * kNbWarps + warp; q < a.nunits; q += (int64_t)gridDim.x * kNbWarps) {
-        const WorkItem U = a.units[q];
-        const PatchDev* P = a.pd + U.patch;
-        const float s_f = P->s_f, sz_f = P->sz_f;
-        const int ncz = P->ncz;
-        const int64_t i = U.begin + lane;
-        const bool valid = i < U.end;
-        LaneState L;
-        L.i = i;
-        float4 r = make_float4(0.f, 0.f, 0.f, 1.f);
-        uint32_t cc = 0;
-        float hf = 1.0f;
-        if (valid) {
-            r = a.r4[i];
-            cc = a.g.cellxyz[i];
-            hf = (float)a.h[i];
-        }
-        const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
-        const float tol = kTolBase + kTolCell * (s_f / hf);
-        L.Ti = r.w;
-        L.flo = 1.0f - tol;
-        L.fhi = 1.0f + tol;
-        unsigned pending = __ballot_sync(0xffffffffu, valid);
-        while (pending) {
-            // reference cell: the first pending lane; the lanes within kSpanMax
-            // cells of it form this pass
-            const int ref = __ffs(pending) - 1;
-            WarpBox B;
-            B.refx = __shfl_sync(0xffffffffu, cx, ref);
-            B.refy = __shfl_sync(0xffffffffu, cy, ref);
-            B.refz = __shfl_sync(0xffffffffu, cz, ref);
-            L.dx = cx - B.refx;
-            L.dy = cy - B.refy;
-            int dz = cz - B.refz;
-            if (dz > ncz / 2) dz -= ncz;
-            else if (dz < -(ncz / 2)) dz += ncz;
-            L.dz = dz;
-            L.kki = (uint32_t)(L.dx + 5 * L.dy + 25 * L.dz) << kColBits;
-            L.act = ((pending >> lane) & 1u) && abs(L.dx) <= kSpanMax && abs(L.dy) <= kSpanMax &&
-                    abs(L.dz) <= kSpanMax;
-            const unsigned actm = __ballot_sync(0xffffffffu, L.act);
-            L.ox = fmaf((float)L.dx, s_f, r.x);
-            L.oy = fmaf((float)L.dy, s_f, r.y);
-            L.oz = fmaf((float)L.dz, sz_f, r.z);
-            B.x0 = warp_min(L.act ? L.ox : 3.4e38f);
-            B.x1 = warp_max(L.act ? L.ox : -3.4e38f);
-            B.y0 = warp_min(L.act ? L.oy : 3.4e38f);
-            B.y1 = warp_max(L.act ? L.oy : -3.4e38f);
-            B.z0 = warp_min(L.act ? L.oz : 3.4e38f);
-            B.z1 = warp_max(L.act ? L.oz : -3.4e38f);
-            B.hw = warp_max(L.act ? hf : 0.0f);
-            L.cnt = 0;
-            L.own = 0;
-            warp_walk<false>(a, P, S, L, lane, B, false, 0);
-            // reserve the rows of this pass in the pool and write them out
-            const uint32_t v = L.act ? L.cnt : 0u;
-            uint32_t inc = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += t;
-            }
-            const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-            unsigned long long base = 0;
-            if (lane == 0) {
-                base = atomicAdd(&a.pool_used[0], (unsigned long long)tot);
-                const unsigned long long before = atomicAdd(&a.pool_used[1], (unsigned long long)tot);
-                if (base + tot > (unsigned long long)a.pool_cap || before + tot > (unsigned long long)a.max_pairs)
-                    atomicOr(a.status, kStOverflow);
-            }
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const unsigned long long r0 = base + (inc - v);
-            const bool fits = base + tot <= (unsigned long long)a.pool_cap;
-            if (L.act) {
-                a.rowstart[i] = r0;
-                a.cnt[i] = L.cnt;
-                a.nown[i] = L.own;
-            }
-            if (fits) {
-                for (int l = 0; l < 32; l++) {
-                    if (!((actm >> l) & 1u)) continue;
-                    const uint32_t len = min(__shfl_sync(0xffffffffu, L.cnt, l), (uint32_t)kRowCap);
-                    const unsigned long long rs = __shfl_sync(0xffffffffu, r0, l);
-                    for (uint32_t k = lane; k < len; k += 32) a.col[rs + k] = S.rows[l * kRowStride + k];
-                }
-                const bool direct = L.act && L.cnt > (uint32_t)kRowCap;
-                if (__ballot_sync(0xffffffffu, direct)) {
-                    // rows longer than the staging slot: same walk, written to the pool
-                    const uint32_t keep_cnt = L.cnt, keep_own = L.own;
-                    L.cnt = 0;
-                    L.own = 0;
-                    warp_walk<true>(a, P, S, L, lane, B, direct, r0);
-                    L.cnt = keep_cnt;
-                    L.own = keep_own;
-                }
-            }
-            __syncwarp();
-            pending &= ~actm;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Thread-per-particle variant: each lane walks the (2K+1)^3 cells around its
-// own cell with its own pruning, in the same loop order as the other lanes of
-// its warp (lanes of one cell load the same candidates at the same time).
-//
-// Rows go straight to the pool.  Each lane reserves its row before the walk,
-// from the row-length hint c (the particle's row length in the previous
-// lists) as c + c/3 + 8 entries -- on a lattice a small change of h adds a
-// whole shell of neighbours at once, up to about a third of the row -- or,
-// without a hint, from a first walk that only counts.  Reservations are
-// rounded up to a multiple of 8 entries, so every row starts on a 32-byte
-// boundary.  Hits
-// collect in a 16-slot ring in shared memory and leave it as whole 32-byte
-// sectors.  A row that outgrows its reservation is walked again into a fresh
-// reservation of its exact (rounded) length.  Shared memory per warp is 2 KB,
-// which leaves the SM's L1 to the candidate gathers.
-// ---------------------------------------------------------------------------
 #ifndef SPH_NB_MINB
 #define SPH_NB_MINB 8                   // resident CTAs per SM the registers are sized for
 #endif
@@ -396,27 +77,79 @@ static_assert(kGroup >= 1 && kGroup <= 8, "a group may fill at most one half of 
 constexpr int kRing = 16;               // ring slots per lane (two halves of 8)
 constexpr uint32_t kHintMargin = 8;     // growth a row may have since the hint, beyond c/3
 
-enum WalkMode { kWalkCount = 0, kWalkRing = 1, kWalkDirect = 2 };
+// Guard band for candidates shifted by up to D cells: the FP32 error of r^2
+// grows with the shift (a term of the cell edge per cell), so the cell term
+// of the band, sized for shifts of up to 3 cells, scales with D / 3 beyond.
+__device__ __forceinline__ float guard_tol(float s_over_h, int D)
+{
+    return kTolBase + kTolCell * s_over_h * fmaxf(1.0f, (float)D * (1.0f / 3.0f));
+}
 
-struct RowOut {
-    uint32_t* col;      // the row's first pool entry
-    uint32_t res;       // entries reserved
-    uint32_t* ring;     // this lane's ring: slot k at ring[32 k]
+enum WalkMode { kWalkRing = 0, kWalkFlat = 1 };
+
+// the row being built by one lane
+struct Row {
+    uint32_t* col;      // the row's first pool entry; flat mode: nullptr = count only
+    uint32_t* ring;     // this lane's ring (ring mode): slot k at ring[32 k]
+    uint32_t res;       // entries reserved (ring mode)
+    uint32_t cnt;       // entries so far
+    uint32_t own;       // n_i so far
 };
 
 __device__ __forceinline__ uint32_t round8(uint32_t v) { return (v + 7u) & ~7u; }
 
-// ring half hf (8 entries) to the pool at row entry blk, as two 16-byte stores
-__device__ __forceinline__ void ring_flush(const RowOut& o, uint32_t hf, uint32_t blk)
+template <int MODE>
+__device__ __forceinline__ void row_put(Row& r, uint32_t w)
 {
-    const uint32_t* rg = o.ring + hf * (8 * 32);
-    uint4* dst = reinterpret_cast<uint4*>(o.col + blk);
-    dst[0] = make_uint4(rg[0], rg[32], rg[64], rg[96]);
-    dst[1] = make_uint4(rg[128], rg[160], rg[192], rg[224]);
+    if (MODE == kWalkRing) r.ring[(r.cnt & (kRing - 1)) * 32] = w;
+    else if (r.col) r.col[r.cnt] = w;
+    r.cnt++;
 }
 
+// after a group of at most 8 puts that started at count c0: at most one half
+// of the ring filled, written out as two 16-byte stores
+template <int MODE>
+__device__ __forceinline__ void row_group_end(Row& r, uint32_t c0)
+{
+    if (MODE == kWalkRing && ((c0 ^ r.cnt) & 8u)) {
+        const uint32_t blk = c0 & ~7u;
+        if (blk + 8u <= r.res) {
+            const uint32_t* rg = r.ring + ((blk >> 3) & 1u) * (8 * 32);
+            uint4* dst = reinterpret_cast<uint4*>(r.col + blk);
+            dst[0] = make_uint4(rg[0], rg[32], rg[64], rg[96]);
+            dst[1] = make_uint4(rg[128], rg[160], rg[192], rg[224]);
+        }
+    }
+}
+
+// the partly filled last sector
+template <int MODE>
+__device__ __forceinline__ void row_finish(Row& r)
+{
+    if (MODE == kWalkRing && r.cnt <= r.res)
+        for (uint32_t k = r.cnt & ~7u; k < r.cnt; k++) r.col[k] = r.ring[(k & (kRing - 1)) * 32];
+}
+
+// a candidate that passed the coarse FP32 test r2 <= T (1 + tol): decide it,
+// exactly inside the guard band
+template <int MODE>
+__device__ __forceinline__ void row_decide(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t j, float r2,
+                                           float Ti, float T, float flo, float fhi, uint32_t w, Row& r)
+{
+    bool in = r2 < T * flo;
+    bool io = r2 < Ti * flo;
+    if (!in || (!io && r2 <= Ti * fhi)) {
+        const int e = exact_pair_at(a, i, j, P->lz);
+        in = e & 1;
+        io = (e >> 1) & 1;
+    }
+    r.own += io;
+    if (in) row_put<MODE>(r, w);
+}
+
+// ---- small i, small j: the (2K+1)^3 fine cells around i's cell ------------
 template <int MODE, int K, int ZW>
-__device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i, const RowOut& o, uint32_t& own)
+__device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, int64_t i, Row& row)
 {
     const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
     const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
@@ -426,13 +159,12 @@ __device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i,
     const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
     const float hf = (float)a.h[i];
     const float Ti = ri.w;
-    const float tol = kTolBase + kTolCell * (s_f / hf);
+    const float tol = guard_tol(s_f / hf, K);
     const float flo = 1.0f - tol, fhi = 1.0f + tol;
     const float slack = (1.0f / 4096.0f) * s_f;
-    const float Rg = 2.0f * fmaxf(hf, P->hmax_f) * (1.0f + 1.0f / 512.0f) + slack;
+    const float Rg = 2.0f * fmaxf(hf, P->hs_f) * (1.0f + 1.0f / 512.0f) + slack;
     const float Rg2 = Rg * Rg;
     const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
-    uint32_t cnt = 0;
     const int nz = ZW ? ncz : 2 * K + 1;
     for (int iz = 0; iz < nz; iz++) {
         int czj, zd;
@@ -499,48 +231,205 @@ __device__ uint32_t thread_walk_k(const NbArgs& a, const PatchDev* P, int64_t i,
                         if (jb + (uint32_t)u < se.y && r2[u] <= T[u] * fhi) near |= 1u << u;
                     }
                     if (!near) continue;
-                    const uint32_t c0 = cnt;
+                    const uint32_t c0 = row.cnt;
 #pragma unroll
                     for (int u = 0; u < kGroup; u++) {
                         if (!(near & (1u << u))) continue;
                         const uint32_t j = jb + (uint32_t)u;
                         if ((int64_t)j == i) continue;
-                        bool in = r2[u] < T[u] * flo;
-                        bool io = r2[u] < Ti * flo;
-                        if (!in || (!io && r2[u] <= Ti * fhi)) {
-                            const int e = exact_pair_at(a, i, j, P->lz);
-                            in = e & 1;
-                            io = (e >> 1) & 1;
-                        }
-                        own += io;
-                        if (!in) continue;
-                        if (MODE == kWalkRing) o.ring[(cnt & (kRing - 1)) * 32] = j | kk;
-                        else if (MODE == kWalkDirect) o.col[cnt] = j | kk;
-                        cnt++;
+                        row_decide<MODE>(a, P, i, j, r2[u], Ti, T[u], flo, fhi, j | kk, row);
                     }
-                    // at most kGroup <= 8 hits per group: at most one half of the ring filled
-                    if (MODE == kWalkRing && ((c0 ^ cnt) & 8u)) {
-                        const uint32_t blk = c0 & ~7u;
-                        if (blk + 8u <= o.res) ring_flush(o, (blk >> 3) & 1u, blk);
-                    }
+                    row_group_end<MODE>(row, c0);
                 }
             }
         }
     }
-    if (MODE == kWalkRing && cnt <= o.res) {
-        // the partly filled last sector
-        const uint32_t blk = cnt & ~7u;
-        for (uint32_t k = blk; k < cnt; k++) o.col[k] = o.ring[(k & (kRing - 1)) * 32];
-    }
-    return cnt;
 }
 
-template <int MODE, int K>
-__device__ __forceinline__ uint32_t thread_walk(const NbArgs& a, const PatchDev* P, int64_t i, const RowOut& o,
-                                                uint32_t& own)
+// stencil code of a neighbour at cell offset (dcx, dcy, dcz): dcz is the
+// signed offset with distinct z cells (zmode 0, |dcz| <= 2 for a code), the
+// z cell count offset modulo ncz when all z cells are visited (zmode 1)
+__device__ __forceinline__ uint32_t stencil_code(const PatchDev* P, int dcx, int dcy, int dcz, bool zsigned)
 {
-    if (P->zmode) return thread_walk_k<MODE, K, 1>(a, P, i, o, own);
-    return thread_walk_k<MODE, K, 0>(a, P, i, o, own);
+    if (dcx < -2 || dcx > 2 || dcy < -2 || dcy > 2) return kFarCode;
+    int zd;
+    if (P->zmode) {
+        zd = dcz % P->ncz;
+        if (zd < 0) zd += P->ncz;
+    } else {
+        if (!zsigned || dcz < -2 || dcz > 2) return kFarCode;
+        zd = dcz + 2;
+    }
+    return (uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd);
+}
+
+// ---- big i, small j: the fine cells within 2 h_i of i ---------------------
+// (rows pass by value through the out-of-line walks, so that the caller's
+// row stays in registers)
+template <int MODE>
+__device__ __noinline__ Row walk_big_fine(const NbArgs& a, const PatchDev* P, int64_t i, Row row)
+{
+    const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
+    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
+    const uint32_t cbase = (uint32_t)P->cell_base;
+    const float4 ri = a.r4[i];
+    const uint32_t cc = a.g.cellxyz[i];
+    const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
+    const float hf = (float)a.h[i];
+    const float Ti = ri.w;
+    const float slack = (1.0f / 4096.0f) * s_f;
+    const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
+    const float Rg = fmaxf(hf, P->hs_f) * Rc + slack;
+    const float Rg2 = Rg * Rg;
+    const int Kb = min((int)ceilf(Rg / s_f), kMaxCellsAxis);
+    const int Kz = min((int)ceilf(Rg / sz_f), kMaxCellsAxis);
+    // a z block longer than the period: every z cell once, minimum image in FP32
+    const bool zw = P->zmode != 0 || 2 * Kz + 1 > ncz;
+    const float tol = guard_tol(s_f / hf, max(Kb, zw ? ncz : Kz));
+    const float flo = 1.0f - tol, fhi = 1.0f + tol;
+    const int nz = zw ? ncz : 2 * Kz + 1;
+    for (int iz = 0; iz < nz; iz++) {
+        int czj, dcz;
+        float gz2 = 0.0f;
+        if (!zw) {
+            dcz = iz - Kz;
+            czj = ((cz + dcz) % ncz + ncz) % ncz;
+            const float g = dcz > 0 ? (float)dcz * sz_f - ri.z : (dcz < 0 ? ri.z - (float)(dcz + 1) * sz_f : 0.0f);
+            const float gg = fmaxf(g, 0.0f);
+            gz2 = gg * gg;
+            if (gz2 >= Rg2) continue;
+        } else {
+            dcz = iz;
+            czj = cz + iz;
+            if (czj >= ncz) czj -= ncz;
+        }
+        const float zo = ri.z - (float)dcz * sz_f;
+        for (int dcy = -Kb; dcy <= Kb; dcy++) {
+            const int cyj = cy + dcy;
+            if ((unsigned)cyj >= (unsigned)ncy) continue;
+            const float g = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : 0.0f);
+            const float gy = fmaxf(g, 0.0f);
+            const float gzy2 = fmaf(gy, gy, gz2);
+            if (gzy2 >= Rg2) continue;
+            const float yo = ri.y - (float)dcy * s_f;
+            const uint32_t lrow = cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx;
+            for (int dcx = -Kb; dcx <= Kb; dcx++) {
+                const int cxj = cx + dcx;
+                if ((unsigned)cxj >= (unsigned)ncx) continue;
+                const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : 0.0f);
+                const float gx = fmaxf(gxr, 0.0f);
+                const float d2 = fmaf(gx, gx, gzy2);
+                if (d2 >= Rg2) continue;
+                const uint32_t lin = lrow + (uint32_t)cxj;
+                const uint2 se = a.g.cse[lin];
+                if (se.x >= se.y) continue;
+                const float xo = ri.x - (float)dcx * s_f;
+                const uint32_t kk = stencil_code(P, dcx, dcy, dcz, !zw) << kColBits;
+                for (uint32_t j = se.x; j < se.y; j++) {
+                    const float4 q = a.r4[j];
+                    const float dx = xo - q.x, dy = yo - q.y;
+                    float dz = zo - q.z;
+                    if (zw) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float T = fmaxf(Ti, q.w);
+                    if (r2 > T * fhi) continue;
+                    const uint32_t c0 = row.cnt;
+                    row_decide<MODE>(a, P, i, j, r2, Ti, T, flo, fhi, j | kk, row);
+                    row_group_end<MODE>(row, c0);
+                }
+            }
+        }
+    }
+    return row;
+}
+
+// ---- any i, big j: the coarse cells around i's coarse cell -----------------
+template <int MODE>
+__device__ __noinline__ Row walk_coarse(const NbArgs& a, const PatchDev* P, int64_t i, Row row)
+{
+    const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
+    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
+    const int kc = P->kc, C = 1 << kc;
+    const int ncxc = P->ncxc, ncyc = P->ncyc, nczc = P->nczc, zmc = P->zmode_c;
+    const float4 ri = a.r4[i];
+    const uint32_t cc = a.g.cellxyz[i];
+    const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
+    const int X = cx >> kc, Y = cy >> kc, Z = cz >> kc;
+    const float hf = (float)a.h[i];
+    const float Ti = ri.w;
+    const float slack = (1.0f / 4096.0f) * s_f;
+    const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
+    const float tol = guard_tol(s_f / hf, 2 * C);
+    const float flo = 1.0f - tol, fhi = 1.0f + tol;
+    const int nzc = zmc ? nczc : 3;
+    for (int iz = 0; iz < nzc; iz++) {
+        int Zw, zshift = 0;   // coarse z cell, and the period shift (fine cells) of its image
+        float gz = 0.0f;
+        if (!zmc) {
+            const int Zu = Z + iz - 1;
+            Zw = Zu < 0 ? Zu + nczc : (Zu >= nczc ? Zu - nczc : Zu);
+            zshift = Zu < 0 ? -ncz : (Zu >= nczc ? ncz : 0);
+            const float lo = (float)(Zw * C + zshift - cz) * sz_f;
+            const float hi = (float)(min(Zw * C + C, ncz) + zshift - cz) * sz_f;
+            gz = fmaxf(fmaxf(lo - ri.z, ri.z - hi), 0.0f);
+        } else {
+            Zw = iz;
+        }
+        for (int Yc = max(Y - 1, 0); Yc <= min(Y + 1, ncyc - 1); Yc++) {
+            const float ylo = (float)(Yc * C - cy) * s_f, yhi = (float)(min(Yc * C + C, ncy) - cy) * s_f;
+            const float gy = fmaxf(fmaxf(ylo - ri.y, ri.y - yhi), 0.0f);
+            for (int Xc = max(X - 1, 0); Xc <= min(X + 1, ncxc - 1); Xc++) {
+                const float xlo = (float)(Xc * C - cx) * s_f, xhi = (float)(min(Xc * C + C, ncx) - cx) * s_f;
+                const float gx = fmaxf(fmaxf(xlo - ri.x, ri.x - xhi), 0.0f);
+                const int64_t lin = P->coarse_base + ((int64_t)Zw * ncyc + Yc) * ncxc + Xc;
+                const uint2 se = a.g.cse[lin];
+                if (se.x >= se.y) continue;
+                const float R = fmaxf(hf, a.g.chmax[lin]) * Rc + slack;
+                if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= R * R) continue;
+                for (uint32_t j = se.x; j < se.y; j++) {
+                    if ((int64_t)j == i) continue;
+                    const uint32_t cj = a.g.cellxyz[j];
+                    const int dcx = (int)(cj & 255) - cx, dcy = (int)((cj >> 8) & 255) - cy;
+                    const int dcz = (int)(cj >> 16) + zshift - cz;
+                    const float4 q = a.r4[j];
+                    const float dx = (ri.x - (float)dcx * s_f) - q.x;
+                    const float dy = (ri.y - (float)dcy * s_f) - q.y;
+                    float dz = (ri.z - (float)dcz * sz_f) - q.z;
+                    if (zmc) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float T = fmaxf(Ti, q.w);
+                    if (r2 > T * fhi) continue;
+                    const uint32_t kk = stencil_code(P, dcx, dcy, dcz, !zmc) << kColBits;
+                    const uint32_t c0 = row.cnt;
+                    row_decide<MODE>(a, P, i, j, r2, Ti, T, flo, fhi, j | kk, row);
+                    row_group_end<MODE>(row, c0);
+                }
+            }
+        }
+    }
+    return row;
+}
+
+// the whole search for particle i
+template <int MODE, int K>
+__device__ __forceinline__ void walk_all(const NbArgs& a, const PatchDev* P, int64_t i, bool big, Row& row)
+{
+    if (!big) {
+        if (P->zmode) walk_small<MODE, K, 1>(a, P, i, row);
+        else walk_small<MODE, K, 0>(a, P, i, row);
+    } else {
+        row = walk_big_fine<MODE>(a, P, i, row);
+    }
+    if (P->nbig > 0) row = walk_coarse<MODE>(a, P, i, row);
+}
+
+// counting walk (col = nullptr) and repair walk (straight to the pool): one
+// out-of-line copy serves both
+template <int K>
+__device__ __noinline__ Row walk_all_flat(const NbArgs& a, const PatchDev* P, int64_t i, bool big, Row row)
+{
+    walk_all<kWalkFlat, K>(a, P, i, big, row);
+    return row;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
@@ -566,13 +455,15 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         const PatchDev* P = a.pd + U.patch;
         const int64_t i = U.begin + lane;
         const bool act = i < U.end;
+        // big particles sit at the end of their patch
+        const bool big = act && i >= P->end - (int64_t)P->nbig;
         // reservation: the hint plus a margin, or the counted length
         uint32_t res = 0;
         if (act) {
             const uint32_t hint = a.rowcap[i];
             if (hint == kNoHint) {
-                uint32_t own0 = 0;
-                res = round8(thread_walk<kWalkCount, K>(a, P, i, RowOut{nullptr, 0u, nullptr}, own0));
+                const Row rc = walk_all_flat<K>(a, P, i, big, Row{nullptr, nullptr, 0u, 0u, 0u});
+                res = round8(rc.cnt);
             } else {
                 const uint32_t c = min(hint, (uint32_t)a.n);
                 res = round8(c + c / 3u + kHintMargin);
@@ -586,25 +477,27 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         const bool ok = base + tot <= pool_cap;
         if (!ok && lane == 0) atomicOr(a.status, kStOverflow);
         unsigned long long r0 = base + (inc - res);
-        uint32_t cnt = 0, own = 0;
-        if (act) cnt = thread_walk<kWalkRing, K>(a, P, i, RowOut{a.col + r0, ok ? res : 0u, ring}, own);
-        if (act && ok && cnt > res) {
+        Row row = {a.col + r0, ring, ok ? res : 0u, 0u, 0u};
+        if (act) {
+            walk_all<kWalkRing, K>(a, P, i, big, row);
+            row_finish<kWalkRing>(row);
+        }
+        if (act && ok && row.cnt > res) {
             // outgrew the reservation: walk again into an exact one
-            const uint32_t need = round8(cnt);
+            const uint32_t need = round8(row.cnt);
             r0 = atomicAdd(&a.pool_used[0], (unsigned long long)need);
             if (r0 + need <= pool_cap) {
-                uint32_t own2 = 0;
-                thread_walk<kWalkDirect, K>(a, P, i, RowOut{a.col + r0, need, nullptr}, own2);
+                walk_all_flat<K>(a, P, i, big, Row{a.col + r0, nullptr, need, 0u, 0u});
             } else {
                 atomicOr(a.status, kStOverflow);
             }
         }
         if (act) {
             a.rowstart[i] = r0;
-            a.cnt[i] = cnt;
-            a.nown[i] = own;
+            a.cnt[i] = row.cnt;
+            a.nown[i] = row.own;
         }
-        const uint32_t listed = __shfl_sync(0xffffffffu, warp_incl_scan(act ? cnt : 0u, lane), 31);
+        const uint32_t listed = __shfl_sync(0xffffffffu, warp_incl_scan(act ? row.cnt : 0u, lane), 31);
         if (lane == 0) {
             const unsigned long long before = atomicAdd(&a.pool_used[1], (unsigned long long)listed);
             if (before + listed > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
@@ -634,24 +527,11 @@ void launch_nb_thread(const Launch& L, const NbArgs& a)
     k_nb_thread<K><<<L.sms * per_sm, 32 * kNbtWarps, smem, L.stream>>>(a);
 }
 
-int launch_nb_lists(const Launch& L, const NbArgs& a, int tpp, int K)
+int launch_nb_lists(const Launch& L, const NbArgs& a, int K)
 {
     if (a.n <= 0 || a.nunits <= 0) return 0;
-    if (tpp == 1) {
-        if (K == 1) launch_nb_thread<1>(L, a);
-        else launch_nb_thread<2>(L, a);
-        return 1;
-    }
-    const size_t smem = sizeof(NbWarpSmem) * kNbWarps;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_nb_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_warp, 32 * kNbWarps, smem);
-    if (per_sm < 1) per_sm = 1;
-    k_nb_warp<<<L.sms * per_sm, 32 * kNbWarps, smem, L.stream>>>(a);
+    if (K == 1) launch_nb_thread<1>(L, a);
+    else launch_nb_thread<2>(L, a);
     return 1;
 }
 

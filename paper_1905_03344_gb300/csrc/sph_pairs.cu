@@ -18,8 +18,9 @@
 // group reduces its partial sums with shuffles.  Mixed precision: positions
 // are FP32 offsets from the particle's cell origin, the column word carries
 // the stencil cell so x_i - x_j = (o_i - o_j) - dc s exactly up to FP32
-// rounding of o; sums are Kahan-compensated FP32.  FP64 path: every pair
-// operation in double.
+// rounding of o (a neighbour beyond the 5 x 5 x 5 stencil, kFarCode, takes dc
+// from both particles' cell coordinates); sums are Kahan-compensated FP32.
+// FP64 path: every pair operation in double.
 #include "sph_internal.cuh"
 
 namespace sphg {
@@ -97,6 +98,21 @@ __device__ __forceinline__ GroupIdx group_idx()
     return g;
 }
 
+// pair separation x_i - x_j for a kFarCode column: the cell offset from both
+// particles' cell coordinates, then the nearest image along z
+__device__ __forceinline__ void rel_dx_far(uint32_t ci, uint32_t cj, float s_f, float sz_f, float lz_f, float oxi,
+                                           float oyi, float ozi, const float4& q, float& dx, float& dy, float& dz)
+{
+    const int dcx = (int)(cj & 255u) - (int)(ci & 255u);
+    const int dcy = (int)((cj >> 8) & 255u) - (int)((ci >> 8) & 255u);
+    const int dcz = (int)(cj >> 16) - (int)(ci >> 16);
+    dx = fmaf(-(float)dcx, s_f, oxi - q.x);
+    dy = fmaf(-(float)dcy, s_f, oyi - q.y);
+    dz = fmaf(-(float)dcz, sz_f, ozi - q.z);
+    if (dz > 0.5f * lz_f) dz -= lz_f;
+    else if (dz < -0.5f * lz_f) dz += lz_f;
+}
+
 // pair separation x_i - x_j from cell-relative FP32 coordinates; ZW = 1 when
 // the patch has fewer than 2K+1 z cells (z offset as a cell count, then the
 // minimum image), ZW = 0 otherwise (signed z offset, no wrap needed)
@@ -120,7 +136,7 @@ __device__ __forceinline__ void rel_dx(const float4& e, float s_f, float sz_f, f
 template <int TPP, int ZW>
 __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                             int gl, float s_f, float sz_f, float lz_f, const float4& ri, float inv2h,
-                                            float& sum, float& comp)
+                                            uint32_t ci, float& sum, float& comp)
 {
     // four neighbours per lane and iteration: the gathers are issued together
     for (uint32_t k = gl; k < len; k += 4 * TPP) {
@@ -132,9 +148,12 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
         for (int u = 0; u < 4; u++) q[u] = a.r.r5[cw[u] & kColMask];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const float4 st = tab[cw[u] >> kColBits];
+            const uint32_t code = cw[u] >> kColBits;
             float dx, dy, dz;
-            rel_dx<ZW>(st, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
+            if (code != kFarCode)
+                rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
+            else
+                rel_dx_far(ci, a.cellxyz[cw[u] & kColMask], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float r = r2 * rsqrtf(r2 + 1e-30f);
             const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
@@ -161,9 +180,10 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
         const float inv2h = a.r.rv[i].w;                   // 1 / (2 h_i)
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
+        const uint32_t ci = a.cellxyz[i];
         float sum = 0.0f, comp = 0.0f;
-        if (P->zmode) density_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, sum, comp);
-        else density_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, sum, comp);
+        if (P->zmode) density_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
+        else density_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
         group_kahan_reduce<TPP>(sum, comp, G.gmask);
         if (G.gl == 0) {
             const float tot = ri.w + (sum - comp);           // self term m_i W(0) ~ m_i
@@ -235,15 +255,10 @@ struct PairTerms {
 
 // one pair of the momentum and energy sums; g scales the whole contribution
 // (m_j, or 0 for a padding lane)
-template <int ZW>
-__device__ __forceinline__ PairTerms momentum_pair(const float4& st, float s_f, float sz_f,
-                                                   float lz_f, const float4& ri, const float4& vi,
-                                                   const float4& ti, float wi5, const float4& q,
-                                                   const float4& vj, const float4& tj, float mj,
-                                                   float alpha, float beta, float eps)
+__device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz, const float4& vi,
+                                                   const float4& ti, float wi5, const float4& vj,
+                                                   const float4& tj, float mj, float alpha, float beta, float eps)
 {
-    float dx, dy, dz;
-    rel_dx<ZW>(st, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
     const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
@@ -276,7 +291,7 @@ template <int TPP, int ZW>
 __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                              int gl, float s_f, float sz_f, float lz_f, const float4& ri,
                                              const float4& vi, const float4& ti, float wi5, float alpha, float beta,
-                                             float eps, MomAcc& A)
+                                             float eps, uint32_t ci, MomAcc& A)
 {
     for (uint32_t k = gl; k < len; k += TPP) {
         const uint32_t cw = row[k];
@@ -284,8 +299,13 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         const float4 q = a.r.r5[j];
         const float4 vj = a.r.rv[j];
         const float4 tj = a.r.rt[j];
-        const PairTerms t = momentum_pair<ZW>(tab[cw >> kColBits], s_f, sz_f, lz_f, ri, vi, ti, wi5, q, vj, tj,
-                                              q.w, alpha, beta, eps);
+        const uint32_t code = cw >> kColBits;
+        float dx, dy, dz;
+        if (code != kFarCode)
+            rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+        else
+            rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+        const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, alpha, beta, eps);
         kahan_add(A.sx, A.cx, t.ax);
         kahan_add(A.sy, A.cy, t.ay);
         kahan_add(A.sz, A.cz, t.az);
@@ -312,11 +332,12 @@ __global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
         const float wi5 = wi2 * wi2 * vi.w;
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
+        const uint32_t ci = a.cellxyz[i];
         MomAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (P->zmode)
-            momentum_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, A);
+            momentum_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, ci, A);
         else
-            momentum_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, A);
+            momentum_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, ci, A);
         group_kahan_reduce<TPP>(A.sx, A.cx, G.gmask);
         group_kahan_reduce<TPP>(A.sy, A.cy, G.gmask);
         group_kahan_reduce<TPP>(A.sz, A.cz, G.gmask);

@@ -97,7 +97,41 @@ __global__ void k_reset_red(int npatch, PatchRed* red)
         red[p].ymax = 0ull;
         red[p].hmax = 0ull;
         red[p].hcmin = ~0ull;
+        for (int b = 0; b < kHBins; b++) red[p].hist[b] = 0u;
     }
+}
+
+// ---------------------------------------------------------------------------
+// A1a': per patch, a histogram of h / h_max in kHBins bins (integer counts,
+// so independent of the order of the atomics); it sets the class threshold.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_h_hist(State s, const WorkItem* items, int nitems, PatchRed* red)
+{
+    __shared__ uint32_t hist[kHBins];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        for (int b = threadIdx.x; b < kHBins; b += blockDim.x) hist[b] = 0u;
+        __syncthreads();
+        const double hmax = unord_f64(red[w.patch].hmax);
+        const double scale = hmax > 0.0 ? (double)kHBins / hmax : 0.0;
+        for (int64_t i = w.begin + threadIdx.x; i < w.end; i += blockDim.x) {
+            const double t = s.h[i] * scale;
+            int b = t >= 0.0 && t < (double)kHBins ? (int)t : kHBins - 1;
+            atomicAdd(&hist[b], 1u);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < kHBins; b += blockDim.x)
+            if (hist[b]) atomicAdd(&red[w.patch].hist[b], hist[b]);
+        __syncthreads();
+    }
+}
+
+int launch_h_hist(const Launch& L, const State& s, const WorkItem* items, int nitems, PatchRed* red)
+{
+    if (nitems <= 0) return 0;
+    int grid = nitems < L.sms * 8 ? nitems : L.sms * 8;
+    k_h_hist<<<grid, 256, 0, L.stream>>>(s, items, nitems, red);
+    return 1;
 }
 
 int launch_reset_red(const Launch& L, int npatch, PatchRed* red)
@@ -107,9 +141,14 @@ int launch_reset_red(const Launch& L, int npatch, PatchRed* red)
 }
 
 // ---------------------------------------------------------------------------
-// A1b: grid of each patch.  Cell edge s = 2 h_max cell_factor (with margin),
-// K = 1 stencil half-extent for cell_factor >= 1, else 2, so K s >= 2 h_max.
-// At most 256 cells per axis and cell_cap cells per patch (s grows if not).
+// A1b: grid of each patch.  Class threshold h_s: the upper edge of the
+// lowest histogram bin above which at most 1/kBigShare of the patch lies (h_s
+// = h_max, no big particles, when that edge is above 0.8 h_max).  Fine cell
+// edge s = 2 h_s cell_factor (with margin), K = 1 stencil half-extent for
+// cell_factor >= 1, else 2, so K s >= 2 h_s.  Coarse cells are aligned blocks
+// of 2^kc fine cells with 2^kc s >= 2 h_max, so the 3 x 3 x 3 coarse block
+// around a particle holds every big particle that can reach it.  At most 128
+// cells per axis and cell_cap fine + coarse cells per patch (s grows if not).
 // Along z: ncz = floor(lz / s) cells of edge lz / ncz; when fewer than 2K+1,
 // every z cell is visited once and the minimum image is taken in FP32.
 // ---------------------------------------------------------------------------
@@ -121,7 +160,8 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
     PatchDev P = pd[p];
     const int K = cell_factor >= 1.0 ? 1 : 2;
     double xmin = 0, ymin = 0, xmax = 0, ymax = 0, hmax = 0;
-    if (P.end > P.begin) {
+    const int64_t np = P.end - P.begin;
+    if (np > 0) {
         xmin = unord_f64(red[p].xmin);
         ymin = unord_f64(red[p].ymin);
         xmax = unord_f64(red[p].xmax);
@@ -137,24 +177,51 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
         ex = ey = 0.0;
         hmax = 0.0;
     }
-    double s = 2.0 * hmax * cell_factor * kCellMargin;
+    // class threshold from the histogram of h / h_max
+    double hs = hmax;
+    {
+        const int64_t allow = np / kBigShare;
+        int64_t above = 0;
+        int b = kHBins - 1;
+        while (b > 0 && above + (int64_t)red[p].hist[b] <= allow) {
+            above += red[p].hist[b];
+            b--;
+        }
+        const double edge = hmax * (double)(b + 1) / (double)kHBins;
+        if (edge < 0.8 * hmax) hs = edge;
+    }
+    double s = 2.0 * hs * cell_factor * kCellMargin;
     const double sext = fmax(ex, ey) / (double)(kMaxCellsAxis - 1) * kCellMargin;
     if (s < sext) s = sext;
     if (!(s > 0.0)) s = P.lz > 0.0 ? P.lz : 1.0;
-    int64_t ncx = 1, ncy = 1, ncz = 1;
-    for (int iter = 0; iter < 200; iter++) {
+    int64_t ncx = 1, ncy = 1, ncz = 1, ncxc = 1, ncyc = 1, nczc = 1;
+    int kc = 0;
+    bool fits = false;
+    for (int iter = 0; iter < 200 && !fits; iter++) {
         ncx = (int64_t)floor(ex / s) + 1;
         ncy = (int64_t)floor(ey / s) + 1;
         ncz = (int64_t)floor(P.lz / s);
         if (ncz < 1) ncz = 1;
         if (ncz > kMaxCellsAxis) ncz = kMaxCellsAxis;
-        if (ncx <= kMaxCellsAxis && ncy <= kMaxCellsAxis && ncx * ncy * ncz <= P.cell_cap) break;
-        s *= 1.25;
+        kc = 0;
+        if (hs < hmax) {
+            while (kc < kMortonBits && (double)(1 << kc) * s < 2.0 * hmax * kCellMargin) kc++;
+            // whole coarse cells along the period (a partial one would let a big
+            // particle two coarse cells away across the wrap reach the block)
+            if (ncz >= (1 << kc)) ncz = (ncz >> kc) << kc;
+        } else {
+            kc = kMortonBits;   // no big particles: one (empty) coarse cell
+        }
+        ncxc = (ncx + (1 << kc) - 1) >> kc;
+        ncyc = (ncy + (1 << kc) - 1) >> kc;
+        nczc = (ncz + (1 << kc) - 1) >> kc;
+        fits = ncx <= kMaxCellsAxis && ncy <= kMaxCellsAxis && ncx * ncy * ncz + ncxc * ncyc * nczc <= P.cell_cap;
+        if (!fits) s *= 1.25;
     }
-    if (!(ncx >= 1 && ncy >= 1 && ncx <= kMaxCellsAxis && ncy <= kMaxCellsAxis &&
-          ncx * ncy * ncz <= P.cell_cap)) {
+    if (!fits || ncx < 1 || ncy < 1) {
         atomicOr(status, kStNonFinite);
-        ncx = ncy = ncz = 1;
+        ncx = ncy = ncz = ncxc = ncyc = nczc = 1;
+        kc = 0;
     }
     P.xmin = xmin;
     P.ymin = ymin;
@@ -172,6 +239,15 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
     P.inv_s_f = (float)(1.0 / s);
     P.inv_sz_f = (float)(1.0 / P.sz);
     P.hmax_f = (float)hmax;
+    P.hs = hs;
+    P.hs_f = (float)hs;
+    P.nbig = 0;
+    P.kc = kc;
+    P.ncxc = (int)ncxc;
+    P.ncyc = (int)ncyc;
+    P.nczc = (int)nczc;
+    P.zmode_c = nczc >= 3 ? 0 : 1;
+    P.coarse_base = P.cell_base + ncx * ncy * ncz;
     pd[p] = P;
 }
 
@@ -183,16 +259,19 @@ int launch_grid_params(const Launch& L, int npatch, const PatchRed* red, PatchDe
 }
 
 // ---------------------------------------------------------------------------
-// A1c: key = patch << 24 | Morton(cx, cy, cz), cell coordinates in FP32 from
-// the FP64 offset to the grid origin (error < 1e-4 cell, inside the margin).
+// A1c: key = patch << 22 | big << 21 | Morton(cx, cy, cz), big = (h > h_s),
+// cell coordinates in FP32 from the FP64 offset to the grid origin (error <
+// 1e-4 cell, inside the margin).  Counts the big particles of each patch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_keys(int64_t n, State s, const uint16_t* patch_of,
-                                              const PatchDev* pd, uint32_t* keys, uint32_t* vals)
+                                              PatchDev* pd, uint32_t* keys, uint32_t* vals)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int p = patch_of[i];
-        const PatchDev* P = pd + p;
+        PatchDev* P = pd + p;
+        const bool big = s.h[i] > P->hs;
+        if (big) atomicAdd(&P->nbig, 1);
         const float tx = (float)(s.x[i] - P->xmin) * P->inv_s_f;
         const float ty = (float)(s.y[i] - P->ymin) * P->inv_s_f;
         const float tz = (float)(s.z[i] + 0.5 * P->lz) * P->inv_sz_f;
@@ -200,14 +279,14 @@ __global__ void __launch_bounds__(256) k_keys(int64_t n, State s, const uint16_t
         cx = min(max(cx, 0), P->ncx - 1);
         cy = min(max(cy, 0), P->ncy - 1);
         cz = min(max(cz, 0), P->ncz - 1);
-        keys[i] = ((uint32_t)p << kPatchShift) | part1by2((uint32_t)cx) |
+        keys[i] = ((uint32_t)p << kPatchShift) | ((uint32_t)big << kClassShift) | part1by2((uint32_t)cx) |
                   (part1by2((uint32_t)cy) << 1) | (part1by2((uint32_t)cz) << 2);
         vals[i] = (uint32_t)i;
     }
 }
 
 int launch_keys(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of,
-                const PatchDev* pd, uint32_t* keys, uint32_t* vals)
+                PatchDev* pd, uint32_t* keys, uint32_t* vals)
 {
     if (n <= 0) return 0;
     k_keys<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, s, patch_of, pd, keys, vals);
@@ -502,7 +581,8 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
         perm_dst[k] = perm_src[si];
         hint.rowcap[k] = have_hint ? hint.cnt_prev[si] : kNoHint;
 
-        const uint32_t mort = key & ((1u << kPatchShift) - 1u);
+        const uint32_t mort = key & kMortonMask;
+        const bool big = (key >> kClassShift) & 1u;
         const uint32_t cx = compact1by2(mort), cy = compact1by2(mort >> 1), cz = compact1by2(mort >> 2);
         g.cellxyz[k] = cx | (cy << 8) | (cz << 16);
         const float ox = (float)(x - (P->xmin + (double)cx * P->s));
@@ -522,10 +602,23 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
             f.vhz[k] = vhz;
             f.invh[k] = 1.0 / h;
         }
-        const int64_t lin = P->cell_base + ((int64_t)cz * P->ncy + cy) * P->ncx + cx;
-        if (k == P->begin || skeys[k - 1] != key) g.cse[lin].x = (uint32_t)k;
-        if (k + 1 == P->end || skeys[k + 1] != key) g.cse[lin].y = (uint32_t)(k + 1);
-        atomicMax((unsigned int*)&g.chmax[lin], __float_as_uint(hf));
+        if (!big) {
+            // fine cell of small particles: bounded by a change of key
+            const int64_t lin = P->cell_base + ((int64_t)cz * P->ncy + cy) * P->ncx + cx;
+            if (k == P->begin || skeys[k - 1] != key) g.cse[lin].x = (uint32_t)k;
+            if (k + 1 == P->end || skeys[k + 1] != key) g.cse[lin].y = (uint32_t)(k + 1);
+            atomicMax((unsigned int*)&g.chmax[lin], __float_as_uint(hf));
+        } else {
+            // coarse cell of big particles: an aligned block of 2^kc fine cells,
+            // contiguous in Morton order, bounded by a change of key >> 3 kc
+            const int kc = P->kc;
+            const int64_t lin = P->coarse_base +
+                                ((int64_t)(cz >> kc) * P->ncyc + (cy >> kc)) * P->ncxc + (cx >> kc);
+            const uint32_t pre = key >> (3 * kc);
+            if (k == P->begin || (skeys[k - 1] >> (3 * kc)) != pre) g.cse[lin].x = (uint32_t)k;
+            if (k + 1 == P->end || (skeys[k + 1] >> (3 * kc)) != pre) g.cse[lin].y = (uint32_t)(k + 1);
+            atomicMax((unsigned int*)&g.chmax[lin], __float_as_uint(hf));
+        }
     }
 }
 

@@ -202,42 +202,55 @@ int launch_conserved_items(const Launch& L, const StepArgs& a)
     return 1;
 }
 
-// one thread per (patch, quantity): compensated sum of the item partials in
-// item order; with advance != 0 (after an update) also closes the step
-__global__ void k_conserved_finalize(StepArgs a, int advance)
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double v)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+// one warp per (patch, quantity): lane l takes the item partials l, l + 32,
+// ... in order with a compensated sum; lane 0 then adds the 32 lane sums in
+// lane order.  The order is fixed, so the result is reproducible.  With
+// advance != 0 (after an update) it also closes the step.
+__global__ void __launch_bounds__(32) k_conserved_finalize(StepArgs a, int advance)
+{
+    const int t = blockIdx.x;
     if (t >= a.npatch * 7) return;
+    const int lane = threadIdx.x;
     const int p = t / 7, q = t % 7;
     PatchDev* P = a.pd + p;
     const bool ok = !(*a.status & kStBad);
     if (advance && !ok) return;
     double s = 0.0, c = 0.0;
-    for (int it = P->item_begin; it < P->item_end; it++) {
-        const double v = a.partials[(int64_t)it * 7 + q];
-        const double tt = s + v;
-        if (fabs(s) >= fabs(v)) c += (s - tt) + v;
-        else c += (v - tt) + s;
-        s = tt;
+    for (int it = P->item_begin + lane; it < P->item_end; it += 32)
+        neumaier_add(s, c, a.partials[(int64_t)it * 7 + q]);
+    double S = 0.0, C = 0.0;
+    for (int l = 0; l < 32; l++) {
+        const double sl = __shfl_sync(0xffffffffu, s, l);
+        const double cl = __shfl_sync(0xffffffffu, c, l);
+        neumaier_add(S, C, sl);
+        C += cl;
     }
-    a.cons[p * 7 + q] = s + c;
-    if (advance && q == 0) {
-        P->dt_prev = P->dt;
-        P->step += 1;
+    if (lane == 0) {
+        a.cons[p * 7 + q] = S + C;
+        if (advance && q == 0) {
+            P->dt_prev = P->dt;
+            P->step += 1;
+        }
     }
 }
 
 int launch_conserved_finalize(const Launch& L, const StepArgs& a)
 {
-    const int nt = a.npatch * 7;
-    k_conserved_finalize<<<(nt + 127) / 128, 128, 0, L.stream>>>(a, 0);
+    k_conserved_finalize<<<a.npatch * 7, 32, 0, L.stream>>>(a, 0);
     return 1;
 }
 
 int launch_step_finalize(const Launch& L, const StepArgs& a)
 {
-    const int nt = a.npatch * 7;
-    k_conserved_finalize<<<(nt + 127) / 128, 128, 0, L.stream>>>(a, 1);
+    k_conserved_finalize<<<a.npatch * 7, 32, 0, L.stream>>>(a, 1);
     return 1;
 }
 

@@ -34,8 +34,30 @@ def near_ties(n=600, seed=5, k=3):
             "m": np.full(N, 1.0 / N), "h": np.full(N, 0.03), "u": np.ones(N)}
 
 
+def h_tail(n, seed, h0, tails, lz=1.0):
+    """Random cloud with most h = h0 and a few larger: tails is a list of
+    (fraction, h_lo, h_hi).  The largest h set apart as big particles, with
+    search reaches across many fine cells and, for long reaches, across the
+    whole z period.  h0 gives about 30 neighbours: with only a handful, rows
+    made of pairs near the edge of a kernel support (q = 1 - r/2h close to
+    0, where FP32 loses relative accuracy) would dominate the mixed-path
+    error of isolated particles."""
+    f = inputs.random_cloud(n, seed=seed, h_lo=h0, h_hi=h0 * 1.1, lz=lz)
+    rng = np.random.default_rng(seed + 100)
+    idx = rng.permutation(n)
+    k0 = 0
+    for frac, lo, hi in tails:
+        k = int(round(frac * n))
+        f["h"][idx[k0:k0 + k]] = rng.uniform(lo, hi, k)
+        k0 += k
+    f["lz"] = lz
+    return f
+
+
 CASES = {
     "patch20": lambda: inputs.square_patch(20),
+    "htail_far": lambda: h_tail(3000, 41, 0.09, [(0.01, 0.3, 0.45), (0.04, 0.12, 0.16)]),
+    "htail_near": lambda: h_tail(12000, 42, 0.08, [(0.01, 0.17, 0.2), (0.03, 0.1, 0.12)], lz=3.0),
     "cloud": lambda: inputs.random_cloud(3000, seed=1),
     "hspread": lambda: inputs.random_cloud(2500, seed=2, h_lo=0.01, h_hi=0.15),
     "irregular": lambda: inputs.irregular_patch(16, seed_pos=3, seed_mass=4),
@@ -50,6 +72,7 @@ def cap_pairs(n):
 
 def run_lists(B, f, **kw):
     n = len(f["x"])
+    kw.setdefault("lz", f.pop("lz", 1.0))
     sim = B.SPH(max(n, 1), max_pairs=cap_pairs(n), **kw)
     sim.set_particles(f)
     sim.find_neighbors()
@@ -64,8 +87,9 @@ def run_lists(B, f, **kw):
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_neighbor_lists_bit_exact(B, orc, case):
     f = CASES[case]()
-    ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
-    o, c, nown, nnb = run_lists(B, f)
+    lz = f.pop("lz", 1.0)
+    ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"], lz)
+    o, c, nown, nnb = run_lists(B, f, lz=lz)
     assert np.array_equal(o, ref.off)
     assert np.array_equal(c, ref.col)
     assert np.array_equal(nown.astype(np.int64), ref.nown.astype(np.int64))
@@ -82,16 +106,17 @@ def test_neighbor_lists_any_launch_shape(B, orc, tpp, cf):
     assert np.array_equal(nown.astype(np.int64), ref.nown.astype(np.int64))
 
 
-def _oracle_forces(orc, f):
-    nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
-    rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+def _oracle_forces(orc, f, lz=1.0):
+    nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"], lz)
+    rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb, lz)
     P, c = orc.eos(rho, f["u"])
     ax, ay, az, du, sa, sdu = orc.momentum_energy(f["x"], f["y"], f["z"], f["vx"], f["vy"], f["vz"],
-                                                  f["m"], f["h"], rho, P, c, nb)
+                                                  f["m"], f["h"], rho, P, c, nb, lz)
     return dict(rho=rho, P=P, c=c, ax=ax, ay=ay, az=az, du=du, sa=sa, sdu=sdu)
 
 
 def _gpu_forces(B, f, precision, **kw):
+    kw.setdefault("lz", 1.0)
     sim = B.SPH(len(f["x"]), precision=precision, max_pairs=cap_pairs(len(f["x"])), **kw)
     sim.set_particles(f)
     sim.find_neighbors()
@@ -104,6 +129,8 @@ def _gpu_forces(B, f, precision, **kw):
 
 FORCE_CASES = {
     "patch20": lambda: inputs.square_patch(20),
+    "htail_far": lambda: h_tail(3000, 43, 0.09, [(0.01, 0.3, 0.45), (0.04, 0.12, 0.16)]),
+    "htail_near": lambda: h_tail(12000, 44, 0.08, [(0.01, 0.17, 0.2), (0.03, 0.1, 0.12)], lz=3.0),
     "cloud_av": lambda: inputs.random_cloud(3000, seed=21, vscale=3.0),
     "irregular": lambda: inputs.irregular_patch(16, seed_pos=6, seed_mass=7),
     "zwrap": lambda: inputs.random_cloud(900, seed=8, h_lo=0.12, h_hi=0.3, vscale=2.0),
@@ -126,14 +153,16 @@ def _check_forces(g, o, tol, report, tag):
 @pytest.mark.parametrize("case", sorted(FORCE_CASES))
 def test_fp64_pair_sums(B, orc, case, report):
     f = FORCE_CASES[case]()
-    _check_forces(_gpu_forces(B, f, "fp64"), _oracle_forces(orc, f), 1e-12, report, "fp64/" + case)
+    lz = f.pop("lz", 1.0)
+    _check_forces(_gpu_forces(B, f, "fp64", lz=lz), _oracle_forces(orc, f, lz), 1e-12, report, "fp64/" + case)
 
 
 @pytest.mark.parametrize("case", sorted(FORCE_CASES))
 @pytest.mark.parametrize("tpp", [4, 8, 32])
 def test_mixed_pair_sums(B, orc, case, tpp, report):
     f = FORCE_CASES[case]()
-    _check_forces(_gpu_forces(B, f, "mixed", threads_per_particle=tpp), _oracle_forces(orc, f), 1e-5,
+    lz = f.pop("lz", 1.0)
+    _check_forces(_gpu_forces(B, f, "mixed", threads_per_particle=tpp, lz=lz), _oracle_forces(orc, f, lz), 1e-5,
                   report, "mixed/%s/tpp%d" % (case, tpp))
 
 
