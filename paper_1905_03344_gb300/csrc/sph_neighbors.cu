@@ -66,7 +66,7 @@ __device__ __noinline__ int exact_pair_at(const NbArgs& a, int64_t i, uint32_t j
 }
 
 #ifndef SPH_NB_MINB
-#define SPH_NB_MINB 8                   // resident CTAs per SM the registers are sized for
+#define SPH_NB_MINB 7                   // resident CTAs per SM the registers are sized for
 #endif
 #ifndef SPH_NB_GROUP
 #define SPH_NB_GROUP 4                  // candidates loaded together per lane

@@ -29,6 +29,13 @@ constexpr double kSigmaW = 21.0 / (16.0 * 3.14159265358979323846);
 constexpr float kSigmaWf = (float)kSigmaW;
 constexpr float k80Sigma = (float)(80.0 * kSigmaW);
 
+#ifndef SPH_MOM_CHUNK
+#define SPH_MOM_CHUNK 1                 // momentum: row words in chunks of four (below)
+#endif
+#ifndef SPH_DEN_CHUNK
+#define SPH_DEN_CHUNK 0                 // density: the same; measured slower there
+#endif
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 {
     const float y = __fsub_rn(v, c);
@@ -138,6 +145,41 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
                                             int gl, float s_f, float sz_f, float lz_f, const float4& ri, float inv2h,
                                             uint32_t ci, float& sum, float& comp)
 {
+#if SPH_DEN_CHUNK
+    // chunks of four row words as in the momentum sum
+    const uint4* row4 = reinterpret_cast<const uint4*>(row);
+    const uint32_t nch = (len + 3u) >> 2;
+    for (uint32_t ch = (uint32_t)gl; ch < nch; ch += TPP) {
+        const uint4 w = row4[ch];
+        const uint32_t base = ch * 4u;
+        // words past the row end (inside the reservation, never written) are
+        // replaced by the chunk's first word, which is in the row
+        uint32_t cw[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int u = 1; u < 4; u++)
+            if (base + (uint32_t)u >= len) cw[u] = w.x;
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = a.r.r5[cw[u] & kColMask];
+        float b = 0.0f;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t code = cw[u] >> kColBits;
+            float dx, dy, dz;
+            if (code != kFarCode)
+                rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
+            else
+                rel_dx_far(ci, a.cellxyz[cw[u] & kColMask], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(r2 + 1e-30f);
+            const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
+            const float q2 = qv * qv;
+            const float m = base + (uint32_t)u < len ? q[u].w : 0.0f;
+            b = fmaf(m, q2 * q2 * fmaf(-4.0f, qv, 5.0f), b);
+        }
+        kahan_add(sum, comp, b);
+    }
+#else
     // four neighbours per lane and iteration: the gathers are issued together
     for (uint32_t k = gl; k < len; k += 4 * TPP) {
         uint32_t cw[4];
@@ -162,6 +204,7 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
             kahan_fma(sum, comp, m, q2 * q2 * fmaf(-4.0f, qv, 5.0f));
         }
     }
+#endif
 }
 
 template <int TPP>
@@ -287,12 +330,56 @@ struct MomAcc {
     float sx, cx, sy, cy, sz, cz, su, cu;
 };
 
+
+// The row in chunks of four words: a lane loads its chunk with one 16-byte
+// load (rows start on 32-byte boundaries and are reserved in multiples of 8
+// words, so a chunk never leaves the reservation) one chunk ahead of its use,
+// sums the chunk's four pair terms plainly and adds that sum with Kahan
+// compensation (the plain sum of four terms errs by at most 3 eps times their
+// magnitudes, the order of one term's own rounding).
 template <int TPP, int ZW>
 __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                              int gl, float s_f, float sz_f, float lz_f, const float4& ri,
                                              const float4& vi, const float4& ti, float wi5, float alpha, float beta,
                                              float eps, uint32_t ci, MomAcc& A)
 {
+#if SPH_MOM_CHUNK
+    const uint4* row4 = reinterpret_cast<const uint4*>(row);
+    const uint32_t nch = (len + 3u) >> 2;
+    uint32_t ch = (uint32_t)gl;
+    uint4 w = ch < nch ? row4[ch] : make_uint4(0u, 0u, 0u, 0u);
+    for (; ch < nch; ch += TPP) {
+        const uint4 wn = ch + TPP < nch ? row4[ch + TPP] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t cws[4] = {w.x, w.y, w.z, w.w};
+        const uint32_t base = ch * 4u;
+        float bx = 0.0f, by = 0.0f, bz = 0.0f, bu = 0.0f;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (base + (uint32_t)u >= len) break;
+            const uint32_t cw = cws[u];
+            const uint32_t j = cw & kColMask;
+            const float4 q = a.r.r5[j];
+            const float4 vj = a.r.rv[j];
+            const float4 tj = a.r.rt[j];
+            const uint32_t code = cw >> kColBits;
+            float dx, dy, dz;
+            if (code != kFarCode)
+                rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+            else
+                rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+            const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, alpha, beta, eps);
+            bx += t.ax;
+            by += t.ay;
+            bz += t.az;
+            bu += t.du;
+        }
+        kahan_add(A.sx, A.cx, bx);
+        kahan_add(A.sy, A.cy, by);
+        kahan_add(A.sz, A.cz, bz);
+        kahan_add(A.su, A.cu, bu);
+        w = wn;
+    }
+#else
     for (uint32_t k = gl; k < len; k += TPP) {
         const uint32_t cw = row[k];
         const uint32_t j = cw & kColMask;
@@ -311,10 +398,14 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         kahan_add(A.sz, A.cz, t.az);
         kahan_add(A.su, A.cu, t.du);
     }
+#endif
 }
 
+#ifndef SPH_MOM_MINB
+#define SPH_MOM_MINB 3                  // resident 256-thread CTAs per SM the registers are sized for
+#endif
 template <int TPP>
-__global__ void __launch_bounds__(256) k_momentum_mixed(PairArgs a)
+__global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a)
 {
     __shared__ float4 tab[kStencilCells];
     fill_stencil_table(tab);
