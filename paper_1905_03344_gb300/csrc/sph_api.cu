@@ -313,12 +313,12 @@ void enqueue_sort(sph_ctx* ctx)
     }
     {
         Phase p(ctx, SPH_PHASE_GATHER);
-        cudaMemsetAsync(ctx->grid.cse, 0, (size_t)ctx->cap_cells * sizeof(uint2), ctx->stream);
-        cudaMemsetAsync(ctx->grid.chmax, 0, (size_t)ctx->cap_cells * sizeof(float), ctx->stream);
+        cudaMemsetAsync(ctx->grid.cell, 0, (size_t)ctx->cap_cells * sizeof(uint4), ctx->stream);
         const int nxt = 1 - ctx->cur;
         ctx->launches += launch_gather(L, ctx->n, ctx->keys, ctx->vals, ctx->st[ctx->cur], ctx->st[nxt],
                                        ctx->perm[ctx->cur], ctx->perm[nxt], ctx->pd, ctx->grid, ctx->rec,
                                        ctx->f64, ctx->mixed, RowHint{ctx->cnt, ctx->hint_ok, ctx->rowcap});
+        ctx->launches += launch_cell_boxes(L, ctx->npatch, ctx->pd, ctx->grid, ctx->rec.r4);
         ctx->cur = nxt;
     }
     ctx->fresh = false;
@@ -624,13 +624,10 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
          dalloc(ctx, ctx->vals_alt, N);
     const size_t hw = radix_hist_words(ctx->cap_n);
     ok = ok && dalloc(ctx, ctx->hist, hw) && dalloc(ctx, ctx->scan32, (size_t)scan_tmp_words((int64_t)hw));
-    uint2* cse = nullptr;
-    float* chmax = nullptr;
+    uint4* cellrec = nullptr;
     uint32_t* cellxyz = nullptr;
-    ok = ok && dalloc(ctx, cse, (size_t)ctx->cap_cells) && dalloc(ctx, chmax, (size_t)ctx->cap_cells) &&
-         dalloc(ctx, cellxyz, N);
-    ctx->grid.cse = cse;
-    ctx->grid.chmax = chmax;
+    ok = ok && dalloc(ctx, cellrec, (size_t)ctx->cap_cells) && dalloc(ctx, cellxyz, N);
+    ctx->grid.cell = cellrec;
     ctx->grid.cellxyz = cellxyz;
     ok = ok && dalloc(ctx, ctx->rec.r4, N);
     if (ctx->mixed) {

@@ -90,10 +90,16 @@ struct State {
     double *x, *y, *z, *vx, *vy, *vz, *m, *h, *u, *du_prev, *axp, *ayp, *azp;
 };
 
+// Cell record, 16 bytes: particles [x, y) of the sorted order (x = y: empty;
+// fine cells hold small particles, coarse cells big ones), z = the largest h
+// in the cell (FP32 bits), w = for fine cells the tight box of the cell's
+// particles, as insets from the cell faces in 1/kBoxQ of the cell edge:
+// bits 0-4 low x, 5-9 high x, 10-14 low y, 15-19 high y, 20-24 low z,
+// 25-29 high z (a particle with offset o lies in [lo, kBoxQ - hi) / kBoxQ of
+// the edge, up to the FP32 rounding of o).
+constexpr int kBoxQ = 32;
 struct Grid {
-    uint2* cse;          // [cell] (start, end) in sorted order, 0/0 = empty; fine
-                         // cells hold small particles, coarse cells big ones
-    float* chmax;        // [cell] largest h (FP32) in the cell
+    uint4* cell;         // [cell] record above
     uint32_t* cellxyz;   // [particle] cx | cy << 8 | cz << 16
     const uint16_t* patch_of;  // [particle] patch index
 };
@@ -181,6 +187,8 @@ int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint3
                   const State& src, const State& dst, const uint32_t* perm_src,
                   uint32_t* perm_dst, const PatchDev* pd, const Grid& g, const Recs& r,
                   const Fp64& f, int mixed, const RowHint& hint);
+// tight boxes of the fine cells (after the gather)
+int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4);
 // temporary words of the device-wide exclusive scan over n values
 int64_t scan_tmp_words(int64_t n);
 

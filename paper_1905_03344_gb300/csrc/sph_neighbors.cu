@@ -147,6 +147,19 @@ __device__ __forceinline__ void row_decide(const NbArgs& a, const PatchDev* P, i
     if (in) row_put<MODE>(r, w);
 }
 
+// squared distance from i to the tight box of a fine cell: g*r are the raw
+// distances from i to the cell's near faces (-1e30 along an axis where i is
+// inside the cell's slab), the insets come from the cell record at the given
+// bit offsets, in units qs = s / kBoxQ (qsz = sz / kBoxQ along z)
+__device__ __forceinline__ float tight_gap2(uint32_t box, float gxr, uint32_t xs, float gyr, uint32_t ys, float gzr,
+                                            uint32_t zs, float qs, float qsz)
+{
+    const float tx = fmaxf(fmaf((float)((box >> xs) & 31u), qs, gxr), 0.0f);
+    const float ty = fmaxf(fmaf((float)((box >> ys) & 31u), qs, gyr), 0.0f);
+    const float tz = fmaxf(fmaf((float)((box >> zs) & 31u), qsz, gzr), 0.0f);
+    return fmaf(tx, tx, fmaf(ty, ty, tz * tz));
+}
+
 // ---- small i, small j: the (2K+1)^3 fine cells around i's cell ------------
 template <int MODE, int K, int ZW>
 __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, int64_t i, Row& row)
@@ -165,18 +178,23 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
     const float Rg = 2.0f * fmaxf(hf, P->hs_f) * (1.0f + 1.0f / 512.0f) + slack;
     const float Rg2 = Rg * Rg;
     const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
+    const float qs = s_f * (1.0f / kBoxQ), qsz = sz_f * (1.0f / kBoxQ);
     const int nz = ZW ? ncz : 2 * K + 1;
     for (int iz = 0; iz < nz; iz++) {
         int czj, zd;
         float zsh, gz2;
+        // raw distance from i to the near z face of the plane (-big: the own plane)
+        float gzr = -1e30f;
+        uint32_t zshift = 20;
         if (!ZW) {
             const int dcz = iz - K;
             czj = cz + dcz;
             if (czj < 0) czj += ncz;
             else if (czj >= ncz) czj -= ncz;
             zsh = (float)dcz * sz_f;
-            const float g = dcz > 0 ? (float)dcz * sz_f - ri.z : (dcz < 0 ? ri.z - (float)(dcz + 1) * sz_f : 0.0f);
-            const float gg = fmaxf(g, 0.0f);
+            if (dcz != 0) gzr = dcz > 0 ? (float)dcz * sz_f - ri.z : ri.z - (float)(dcz + 1) * sz_f;
+            zshift = dcz > 0 ? 20u : 25u;
+            const float gg = fmaxf(gzr, 0.0f);
             gz2 = gg * gg;
             zd = dcz + 2;
         } else {
@@ -191,8 +209,9 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
         for (int dcy = -K; dcy <= K; dcy++) {
             const int cyj = cy + dcy;
             if ((unsigned)cyj >= (unsigned)ncy) continue;
-            const float g = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : 0.0f);
-            const float gy = fmaxf(g, 0.0f);
+            const float gyr = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : -1e30f);
+            const uint32_t yshift = dcy > 0 ? 10u : 15u;
+            const float gy = fmaxf(gyr, 0.0f);
             const float gzy2 = fmaf(gy, gy, gz2);
             if (gzy2 >= Rg2) continue;
             const float yo = ri.y - (float)dcy * s_f;
@@ -202,16 +221,16 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
 #pragma unroll 1
             for (int dcx = -K; dcx <= K; dcx++) {
                 if ((unsigned)(cx + dcx) >= (unsigned)ncx) continue;
-                const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : 0.0f);
+                const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : -1e30f);
                 const float gx = fmaxf(gxr, 0.0f);
                 const float d2 = fmaf(gx, gx, gzy2);
                 if (d2 >= Rg2) continue;
                 const uint32_t lin = lrow + (uint32_t)dcx;
-                const uint2 se = a.g.cse[lin];
-                const float hc = a.g.chmax[lin];
+                const uint4 cr = a.g.cell[lin];
+                const uint2 se = make_uint2(cr.x, cr.y);
                 if (se.x >= se.y) continue;
-                const float R = fmaxf(hf, hc) * Rc + slack;
-                if (d2 >= R * R) continue;
+                const float R = fmaxf(hf, __uint_as_float(cr.z)) * Rc + slack;
+                if (tight_gap2(cr.w, gxr, dcx > 0 ? 0u : 5u, gyr, yshift, gzr, zshift, qs, qsz) >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
                 const uint32_t kk = (kkrow + (uint32_t)dcx) << kColBits;
                 // kGroup candidates per iteration: their gathers are in flight together
@@ -321,7 +340,8 @@ __device__ __noinline__ Row walk_big_fine(const NbArgs& a, const PatchDev* P, in
                 const float d2 = fmaf(gx, gx, gzy2);
                 if (d2 >= Rg2) continue;
                 const uint32_t lin = lrow + (uint32_t)cxj;
-                const uint2 se = a.g.cse[lin];
+                const uint4 cr = a.g.cell[lin];
+                const uint2 se = make_uint2(cr.x, cr.y);
                 if (se.x >= se.y) continue;
                 const float xo = ri.x - (float)dcx * s_f;
                 const uint32_t kk = stencil_code(P, dcx, dcy, dcz, !zw) << kColBits;
@@ -382,9 +402,10 @@ __device__ __noinline__ Row walk_coarse(const NbArgs& a, const PatchDev* P, int6
                 const float xlo = (float)(Xc * C - cx) * s_f, xhi = (float)(min(Xc * C + C, ncx) - cx) * s_f;
                 const float gx = fmaxf(fmaxf(xlo - ri.x, ri.x - xhi), 0.0f);
                 const int64_t lin = P->coarse_base + ((int64_t)Zw * ncyc + Yc) * ncxc + Xc;
-                const uint2 se = a.g.cse[lin];
+                const uint4 cr = a.g.cell[lin];
+                const uint2 se = make_uint2(cr.x, cr.y);
                 if (se.x >= se.y) continue;
-                const float R = fmaxf(hf, a.g.chmax[lin]) * Rc + slack;
+                const float R = fmaxf(hf, __uint_as_float(cr.z)) * Rc + slack;
                 if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= R * R) continue;
                 for (uint32_t j = se.x; j < se.y; j++) {
                     if ((int64_t)j == i) continue;

@@ -35,6 +35,9 @@ constexpr float k80Sigma = (float)(80.0 * kSigmaW);
 #ifndef SPH_DEN_CHUNK
 #define SPH_DEN_CHUNK 0                 // density: the same; measured slower there
 #endif
+#ifndef SPH_ROW_PREFETCH
+#define SPH_ROW_PREFETCH 1              // L2 prefetch of the next particle's row
+#endif
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 {
@@ -136,6 +139,34 @@ __device__ __forceinline__ void rel_dx(const float4& e, float s_f, float sz_f, f
     }
 }
 
+// The list words stream from HBM (the pool is far larger than L2).  Each
+// group asks L2 for the row of the particle it takes next -- the group's lanes
+// cover it in 128-byte lines -- while it works on the current one; the start
+// of that row was read one particle earlier, so the request does not wait.
+struct RowAhead {
+    unsigned long long start;
+    uint32_t len;
+};
+
+__device__ __forceinline__ RowAhead row_ahead_read(const PairArgs& a, int64_t i)
+{
+    RowAhead r = {0ull, 0u};
+    if (i < a.n) {
+        r.start = a.rowstart[i];
+        r.len = a.cnt[i];
+    }
+    return r;
+}
+
+template <int TPP>
+__device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowAhead& r, int gl)
+{
+#if SPH_ROW_PREFETCH
+    for (uint32_t o = (uint32_t)gl * 32u; o < r.len; o += TPP * 32u)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.col + r.start + o));
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // A5 + A6, mixed precision
 // ---------------------------------------------------------------------------
@@ -216,7 +247,11 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const float gam = (float)a.gamma;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+    RowAhead ahead = row_ahead_read(a, i0 + gs);
+    for (int64_t i = i0; i < a.n; i += gs) {
+        row_ahead_prefetch<TPP>(a, ahead, G.gl);
+        ahead = row_ahead_read(a, i + 2 * gs);
         const PatchDev* P = a.pd + a.patch_of[i];
         const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
         const float4 ri = a.r.r5[i];
@@ -296,25 +331,34 @@ struct PairTerms {
     float ax, ay, az, du;
 };
 
-// one pair of the momentum and energy sums; g scales the whole contribution
-// (m_j, or 0 for a padding lane)
+// Per-particle constants of the momentum and energy sums.  The viscosity is
+// written with sums instead of means (h_i + h_j = 2 hbar, c_i + c_j = 2 cbar,
+// rho_i + rho_j = 2 rhobar), so that with m2 = (h_i + h_j) v.x / (r^2 +
+// eps/4 (h_i + h_j)^2) = 2 mu,
+//   Pi = mu (beta mu - alpha cbar) / rhobar
+//      = m2 ((beta/2) m2 - (alpha/2)(c_i + c_j)) / (rho_i + rho_j).
+struct MomConst {
+    float eps4, beta2, alpha2;   // eps/4, beta/2, alpha/2
+};
+
+// one pair of the momentum and energy sums, from x_i - x_j = (dx, dy, dz);
+// w^5 q^3 = w^2 (w q)^3 with w q = w - r w^2
 __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz, const float4& vi,
                                                    const float4& ti, float wi5, const float4& vj,
-                                                   const float4& tj, float mj, float alpha, float beta, float eps)
+                                                   const float4& tj, float mj, const MomConst& K)
 {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
     const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
-    const float qj = fmaxf(fmaf(-r, vj.w, 1.0f), 0.0f);
     const float wj2 = vj.w * vj.w;
-    const float wj5 = wj2 * wj2 * vj.w;
-    const float F = fmaf(wj5, qj * qj * qj, wi5 * (qi * qi * qi));
+    const float aj = fmaxf(fmaf(-r, wj2, vj.w), 0.0f);          // w_j q_j
+    const float F = fmaf(wi5, qi * qi * qi, wj2 * (aj * aj * aj));
     const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const float vdot = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-    const float hbar = 0.5f * (ti.w + tj.w);
-    const float mu = __fdividef(hbar * vdot, fmaf(eps * hbar, hbar, r2));
+    const float hs = ti.w + tj.w;
+    const float m2 = __fdividef(hs * vdot, fmaf(K.eps4 * hs, hs, r2));
     const float pi_ = vdot < 0.0f
-                          ? __fdividef(mu * fmaf(beta, mu, -alpha * 0.5f * (ti.z + tj.z)), 0.5f * (ti.x + tj.x))
+                          ? __fdividef(m2 * fmaf(K.beta2, m2, -K.alpha2 * (ti.z + tj.z)), ti.x + tj.x)
                           : 0.0f;
     const float g = mj * F;
     const float fa = g * (ti.y + tj.y + pi_);
@@ -340,8 +384,8 @@ struct MomAcc {
 template <int TPP, int ZW>
 __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                              int gl, float s_f, float sz_f, float lz_f, const float4& ri,
-                                             const float4& vi, const float4& ti, float wi5, float alpha, float beta,
-                                             float eps, uint32_t ci, MomAcc& A)
+                                             const float4& vi, const float4& ti, float wi5, const MomConst& K,
+                                             uint32_t ci, MomAcc& A)
 {
 #if SPH_MOM_CHUNK
     const uint4* row4 = reinterpret_cast<const uint4*>(row);
@@ -367,7 +411,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
                 rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
             else
                 rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-            const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, alpha, beta, eps);
+            const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K);
             bx += t.ax;
             by += t.ay;
             bz += t.az;
@@ -392,7 +436,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
             rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
         else
             rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-        const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, alpha, beta, eps);
+        const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K);
         kahan_add(A.sx, A.cx, t.ax);
         kahan_add(A.sy, A.cy, t.ay);
         kahan_add(A.sz, A.cz, t.az);
@@ -412,8 +456,12 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
     if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
-    const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+    const MomConst K = {0.25f * (float)a.eps, 0.5f * (float)a.beta, 0.5f * (float)a.alpha};
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+    RowAhead ahead = row_ahead_read(a, i0 + gs);
+    for (int64_t i = i0; i < a.n; i += gs) {
+        row_ahead_prefetch<TPP>(a, ahead, G.gl);
+        ahead = row_ahead_read(a, i + 2 * gs);
         const PatchDev* P = a.pd + a.patch_of[i];
         const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
         const float4 ri = a.r.r5[i];
@@ -426,9 +474,9 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
         const uint32_t ci = a.cellxyz[i];
         MomAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (P->zmode)
-            momentum_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, ci, A);
+            momentum_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
         else
-            momentum_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, alpha, beta, eps, ci, A);
+            momentum_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
         group_kahan_reduce<TPP>(A.sx, A.cx, G.gmask);
         group_kahan_reduce<TPP>(A.sy, A.cy, G.gmask);
         group_kahan_reduce<TPP>(A.sz, A.cz, G.gmask);

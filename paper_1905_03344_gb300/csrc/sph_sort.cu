@@ -605,9 +605,9 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
         if (!big) {
             // fine cell of small particles: bounded by a change of key
             const int64_t lin = P->cell_base + ((int64_t)cz * P->ncy + cy) * P->ncx + cx;
-            if (k == P->begin || skeys[k - 1] != key) g.cse[lin].x = (uint32_t)k;
-            if (k + 1 == P->end || skeys[k + 1] != key) g.cse[lin].y = (uint32_t)(k + 1);
-            atomicMax((unsigned int*)&g.chmax[lin], __float_as_uint(hf));
+            if (k == P->begin || skeys[k - 1] != key) g.cell[lin].x = (uint32_t)k;
+            if (k + 1 == P->end || skeys[k + 1] != key) g.cell[lin].y = (uint32_t)(k + 1);
+            atomicMax(&g.cell[lin].z, __float_as_uint(hf));
         } else {
             // coarse cell of big particles: an aligned block of 2^kc fine cells,
             // contiguous in Morton order, bounded by a change of key >> 3 kc
@@ -615,9 +615,9 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
             const int64_t lin = P->coarse_base +
                                 ((int64_t)(cz >> kc) * P->ncyc + (cy >> kc)) * P->ncxc + (cx >> kc);
             const uint32_t pre = key >> (3 * kc);
-            if (k == P->begin || (skeys[k - 1] >> (3 * kc)) != pre) g.cse[lin].x = (uint32_t)k;
-            if (k + 1 == P->end || (skeys[k + 1] >> (3 * kc)) != pre) g.cse[lin].y = (uint32_t)(k + 1);
-            atomicMax((unsigned int*)&g.chmax[lin], __float_as_uint(hf));
+            if (k == P->begin || (skeys[k - 1] >> (3 * kc)) != pre) g.cell[lin].x = (uint32_t)k;
+            if (k + 1 == P->end || (skeys[k + 1] >> (3 * kc)) != pre) g.cell[lin].y = (uint32_t)(k + 1);
+            atomicMax(&g.cell[lin].z, __float_as_uint(hf));
         }
     }
 }
@@ -630,6 +630,50 @@ int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint3
     if (n <= 0) return 0;
     k_gather<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, skeys, svals, src, dst, perm_src,
                                                                  perm_dst, pd, g, r, f, mixed, hint);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// A3': the tight box of each non-empty fine cell, from its particles' FP32
+// offsets, quantised outward to 1/kBoxQ of the cell edge (see Grid).  One
+// thread per cell; blockIdx.y is the patch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int box_q(float o, float inv_edge)
+{
+    const int q = (int)floorf(o * inv_edge * (float)kBoxQ);
+    return min(max(q, 0), kBoxQ - 1);
+}
+
+__global__ void __launch_bounds__(256) k_cell_boxes(const PatchDev* pd, Grid g, const float4* r4)
+{
+    const PatchDev* P = pd + blockIdx.y;
+    const int64_t nfine = (int64_t)P->ncx * P->ncy * P->ncz;
+    const float inv_s = P->inv_s_f, inv_sz = P->inv_sz_f;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nfine; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lin = P->cell_base + c;
+        const uint32_t b = g.cell[lin].x, e = g.cell[lin].y;
+        if (b >= e) continue;
+        int lx = kBoxQ, ly = kBoxQ, lz = kBoxQ, hx = 0, hy = 0, hz = 0;
+        for (uint32_t k = b; k < e; k++) {
+            const float4 q = r4[k];
+            const int qx = box_q(q.x, inv_s), qy = box_q(q.y, inv_s), qz = box_q(q.z, inv_sz);
+            lx = min(lx, qx);
+            ly = min(ly, qy);
+            lz = min(lz, qz);
+            hx = max(hx, qx + 1);
+            hy = max(hy, qy + 1);
+            hz = max(hz, qz + 1);
+        }
+        g.cell[lin].w = (uint32_t)lx | ((uint32_t)(kBoxQ - hx) << 5) | ((uint32_t)ly << 10) |
+                        ((uint32_t)(kBoxQ - hy) << 15) | ((uint32_t)lz << 20) | ((uint32_t)(kBoxQ - hz) << 25);
+    }
+}
+
+int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4)
+{
+    if (npatch <= 0) return 0;
+    const int bx = npatch > 8 ? 8 : (L.sms * 4 + npatch - 1) / npatch;
+    k_cell_boxes<<<dim3((unsigned)bx, (unsigned)npatch), 256, 0, L.stream>>>(pd, g, r4);
     return 1;
 }
 
