@@ -187,8 +187,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--cell-factor", type=float, default=0.0,
+                    help="fixed cell factor (implies --no-autotune); 0 = tuned")
+    ap.add_argument("--tpp", type=int, default=0,
+                    help="fixed lanes per particle of the pair sums (implies --no-autotune); 0 = tuned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.cell_factor or args.tpp:
+        args.no_autotune = True
     if args.impl == "reference":
         return run_reference(args)
 
@@ -211,8 +217,13 @@ def main():
     dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
 
     def make(precision, graph=False):
+        kw = {}
+        if args.cell_factor:
+            kw["cell_factor"] = args.cell_factor
+        if args.tpp:
+            kw["threads_per_particle"] = args.tpp
         sim = binding.SPH(n, precision=precision, stream=stream.cuda_stream,
-                          use_graph=int(graph), max_pairs=int(160 * n))
+                          use_graph=int(graph), max_pairs=int(160 * n), **kw)
         sim.set_particles(dfields)
         return sim
 

@@ -82,7 +82,8 @@ typedef struct {
     double dt_fixed;        /* > 0: fixed dt instead of the Courant condition */
     int32_t adapt_h;        /* 1: h adaptation after each step */
     int32_t threads_per_particle; /* 0 = auto; else 1, 2, 4, 8, 16 or 32 */
-    double cell_factor;     /* cell edge = 2 h_max * cell_factor, in [0.5, 4] */
+    double cell_factor;     /* cell edge = 2 h_s * cell_factor, in [1/3, 4]
+                               (h_s: the patch's class threshold of h) */
     int64_t max_particles;  /* capacity, <= 2^25 */
     int64_t max_pairs;      /* neighbour-list capacity (total list entries);
                                0 = 160 * max_particles.  The list pool holds

@@ -335,7 +335,7 @@ void enqueue_lists(sph_ctx* ctx)
     ctx->canon_valid = false;
     {
         Phase p(ctx, SPH_PHASE_NB);
-        ctx->launches += launch_nb_lists(L, a, ctx->cell_factor >= 1.0 ? 1 : 2);
+        ctx->launches += launch_nb_lists(L, a, stencil_k(ctx->cell_factor));
     }
     // the row lengths now belong to the current order: hints for the next sort
     cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
@@ -565,8 +565,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     if (cfg.max_patches < 1 || cfg.max_patches > kMaxPatches)
         return fail(nullptr, SPH_EINVAL, "max_patches must be in [1, 256]");
     if (cfg.cell_factor == 0.0) cfg.cell_factor = 0.5;
-    if (!(cfg.cell_factor >= 0.5 && cfg.cell_factor <= 4.0))
-        return fail(nullptr, SPH_EINVAL, "cell_factor must be in [0.5, 4]");
+    if (!(cfg.cell_factor >= 1.0 / 3.0 && cfg.cell_factor <= 4.0))
+        return fail(nullptr, SPH_EINVAL, "cell_factor must be in [1/3, 4]");
     const int t = cfg.threads_per_particle;
     if (!(t == 0 || t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32))
         return fail(nullptr, SPH_EINVAL, "threads_per_particle must be 0, 1, 2, 4, 8, 16 or 32");
@@ -1062,7 +1062,7 @@ sph_status sph_autotune(sph_ctx* ctx)
     const bool prof0 = ctx->prof;
     ctx->prof = false;
     destroy_graphs(ctx);
-    const double factors[3] = {0.5, 0.75, 1.0};
+    const double factors[4] = {1.0 / 3.0, 0.5, 0.75, 1.0};
     const int pair_tpps[4] = {4, 8, 16, 32};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -49,6 +49,11 @@ constexpr int kStBad = kStOverflow | kStNonFinite | kStTimeout;  // later phases
 // a margin of more than 4x.
 constexpr float kTolBase = 1.0f / 8192.0f;
 constexpr float kTolCell = 1.0f / 65536.0f;
+// stencil half-extent for a cell factor: K s >= 2 h_s needs K cell_factor >= 1
+__host__ __device__ __forceinline__ int stencil_k(double cell_factor)
+{
+    return cell_factor >= 1.0 ? 1 : (cell_factor >= 0.5 ? 2 : 3);
+}
 // Cell edges carry a relative margin so that FP32 cell assignment can never
 // separate two particles closer than 2 h_max by more than K cells.
 constexpr double kCellMargin = 1.0 + 1.0 / 1024.0;

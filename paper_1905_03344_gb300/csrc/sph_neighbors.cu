@@ -147,6 +147,24 @@ __device__ __forceinline__ void row_decide(const NbArgs& a, const PatchDev* P, i
     if (in) row_put<MODE>(r, w);
 }
 
+// stencil code of a neighbour at cell offset (dcx, dcy, dcz): dcz is the
+// signed offset with distinct z cells (zmode 0, |dcz| <= 2 for a code), the
+// z cell count offset modulo ncz when all z cells are visited (zmode 1)
+__device__ __forceinline__ uint32_t stencil_code(const PatchDev* P, int dcx, int dcy, int dcz, bool zsigned)
+{
+    if (dcx < -2 || dcx > 2 || dcy < -2 || dcy > 2) return kFarCode;
+    int zd;
+    if (P->zmode) {
+        zd = dcz % P->ncz;
+        if (zd < 0) zd += P->ncz;
+        if (zd > 4) return kFarCode;
+    } else {
+        if (!zsigned || dcz < -2 || dcz > 2) return kFarCode;
+        zd = dcz + 2;
+    }
+    return (uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd);
+}
+
 // squared distance from i to the tight box of a fine cell: g*r are the raw
 // distances from i to the cell's near faces (-1e30 along an axis where i is
 // inside the cell's slab), the insets come from the cell record at the given
@@ -172,7 +190,8 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
     const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
     const float hf = (float)a.h[i];
     const float Ti = ri.w;
-    const float tol = guard_tol(s_f / hf, K);
+    // every z cell visited (ZW): shifts of up to ncz - 1 cells along z
+    const float tol = guard_tol(s_f / hf, ZW ? max(K, ncz) : K);
     const float flo = 1.0f - tol, fhi = 1.0f + tol;
     const float slack = (1.0f / 4096.0f) * s_f;
     const float Rg = 2.0f * fmaxf(hf, P->hs_f) * (1.0f + 1.0f / 512.0f) + slack;
@@ -232,7 +251,9 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
                 const float R = fmaxf(hf, __uint_as_float(cr.z)) * Rc + slack;
                 if (tight_gap2(cr.w, gxr, dcx > 0 ? 0u : 5u, gyr, yshift, gzr, zshift, qs, qsz) >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
-                const uint32_t kk = (kkrow + (uint32_t)dcx) << kColBits;
+                // offsets of up to 2 cells have a stencil code; K = 3 reaches 3
+                const uint32_t kk = (K <= 2 ? kkrow + (uint32_t)dcx
+                                            : stencil_code(P, dcx, dcy, ZW ? zd : zd - 2, !ZW)) << kColBits;
                 // kGroup candidates per iteration: their gathers are in flight together
                 for (uint32_t jb = se.x; jb < se.y; jb += kGroup) {
                     float4 q[kGroup];
@@ -263,23 +284,6 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
             }
         }
     }
-}
-
-// stencil code of a neighbour at cell offset (dcx, dcy, dcz): dcz is the
-// signed offset with distinct z cells (zmode 0, |dcz| <= 2 for a code), the
-// z cell count offset modulo ncz when all z cells are visited (zmode 1)
-__device__ __forceinline__ uint32_t stencil_code(const PatchDev* P, int dcx, int dcy, int dcz, bool zsigned)
-{
-    if (dcx < -2 || dcx > 2 || dcy < -2 || dcy > 2) return kFarCode;
-    int zd;
-    if (P->zmode) {
-        zd = dcz % P->ncz;
-        if (zd < 0) zd += P->ncz;
-    } else {
-        if (!zsigned || dcz < -2 || dcz > 2) return kFarCode;
-        zd = dcz + 2;
-    }
-    return (uint32_t)((dcx + 2) + 5 * (dcy + 2) + 25 * zd);
 }
 
 // ---- big i, small j: the fine cells within 2 h_i of i ---------------------
@@ -552,7 +556,8 @@ int launch_nb_lists(const Launch& L, const NbArgs& a, int K)
 {
     if (a.n <= 0 || a.nunits <= 0) return 0;
     if (K == 1) launch_nb_thread<1>(L, a);
-    else launch_nb_thread<2>(L, a);
+    else if (K == 2) launch_nb_thread<2>(L, a);
+    else launch_nb_thread<3>(L, a);
     return 1;
 }
 

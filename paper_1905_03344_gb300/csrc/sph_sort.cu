@@ -144,8 +144,8 @@ int launch_reset_red(const Launch& L, int npatch, PatchRed* red)
 // A1b: grid of each patch.  Class threshold h_s: the upper edge of the
 // lowest histogram bin above which at most 1/kBigShare of the patch lies (h_s
 // = h_max, no big particles, when that edge is above 0.8 h_max).  Fine cell
-// edge s = 2 h_s cell_factor (with margin), K = 1 stencil half-extent for
-// cell_factor >= 1, else 2, so K s >= 2 h_s.  Coarse cells are aligned blocks
+// edge s = 2 h_s cell_factor (with margin), stencil half-extent K = 1 for
+// cell_factor >= 1, 2 for >= 1/2, else 3, so K s >= 2 h_s.  Coarse cells are aligned blocks
 // of 2^kc fine cells with 2^kc s >= 2 h_max, so the 3 x 3 x 3 coarse block
 // around a particle holds every big particle that can reach it.  At most 128
 // cells per axis and cell_cap fine + coarse cells per patch (s grows if not).
@@ -158,7 +158,7 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npatch) return;
     PatchDev P = pd[p];
-    const int K = cell_factor >= 1.0 ? 1 : 2;
+    const int K = stencil_k(cell_factor);
     double xmin = 0, ymin = 0, xmax = 0, ymax = 0, hmax = 0;
     const int64_t np = P.end - P.begin;
     if (np > 0) {

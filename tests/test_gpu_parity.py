@@ -97,7 +97,7 @@ def test_neighbor_lists_bit_exact(B, orc, case):
 
 
 @pytest.mark.parametrize("tpp", [1, 2, 4, 8, 16, 32])
-@pytest.mark.parametrize("cf", [0.5, 0.75, 1.0, 2.5])
+@pytest.mark.parametrize("cf", [1.0 / 3.0, 0.5, 0.75, 1.0, 2.5])
 def test_neighbor_lists_any_launch_shape(B, orc, tpp, cf):
     f = inputs.random_cloud(1500, seed=11, h_lo=0.02, h_hi=0.1)
     ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
@@ -164,6 +164,16 @@ def test_mixed_pair_sums(B, orc, case, tpp, report):
     lz = f.pop("lz", 1.0)
     _check_forces(_gpu_forces(B, f, "mixed", threads_per_particle=tpp, lz=lz), _oracle_forces(orc, f, lz), 1e-5,
                   report, "mixed/%s/tpp%d" % (case, tpp))
+
+
+@pytest.mark.parametrize("case", sorted(FORCE_CASES))
+def test_mixed_pair_sums_small_cells(B, orc, case, report):
+    """Cells of a third of 2 h_s: neighbours three cells away carry the far
+    column code and take their offsets from the cell coordinates."""
+    f = FORCE_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    _check_forces(_gpu_forces(B, f, "mixed", threads_per_particle=4, cell_factor=1.0 / 3.0, lz=lz),
+                  _oracle_forces(orc, f, lz), 1e-5, report, "mixed/%s/cf1_3" % case)
 
 
 def _compare_state(g, o, tol, what):
