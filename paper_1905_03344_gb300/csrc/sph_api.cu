@@ -3,6 +3,7 @@
 // checkpoints and the launch autotuner.  All device work is issued on the
 // context's stream; the kernels live in sph_sort.cu, sph_neighbors.cu,
 // sph_pairs.cu and sph_step.cu.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -97,6 +98,7 @@ struct sph_ctx {
     PatchRed* red = nullptr;
     WorkItem* items = nullptr;
     double *partials = nullptr, *cons = nullptr, *scratch = nullptr;
+    double* hfac = nullptr;        // h-adaptation factors by neighbour count
     int* status = nullptr;
     int* h_status = nullptr;     // pinned
     unsigned long long* pair_acc = nullptr;  // sum of |N| over the steps taken
@@ -285,6 +287,7 @@ StepArgs step_args(sph_ctx* ctx)
     a.n_target = ctx->cfg.n_target;
     a.adapt_h = ctx->cfg.adapt_h;
     a.mixed = ctx->mixed;
+    a.hfac = ctx->hfac;
     a.partials = ctx->partials;
     a.cons = ctx->cons;
     a.status = ctx->status;
@@ -648,7 +651,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ok = ok && dalloc(ctx, ctx->pd, (size_t)ctx->cap_patch) && dalloc(ctx, ctx->red, (size_t)ctx->cap_patch) &&
          dalloc(ctx, ctx->items, (size_t)ctx->cap_items) && dalloc(ctx, ctx->partials, (size_t)ctx->cap_items * 7) &&
          dalloc(ctx, ctx->cons, (size_t)ctx->cap_patch * 7) && dalloc(ctx, ctx->scratch, N) &&
-         dalloc(ctx, ctx->status, 1) && dalloc(ctx, ctx->pair_acc, 1);
+         dalloc(ctx, ctx->status, 1) && dalloc(ctx, ctx->pair_acc, 1) && dalloc(ctx, ctx->hfac, (size_t)kHFacN);
     ctx->grid.patch_of = ctx->patch_of;
     if (ok && cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
@@ -657,6 +660,17 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     }
     cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
     cudaMemsetAsync(ctx->pair_acc, 0, sizeof(unsigned long long), ctx->stream);
+    {
+        // R10: h <- h (1 + (n_target / n)^(1/3)) / 2, the factor for each count
+        // below kHFacN in FP64 on the host
+        std::vector<double> fac(kHFacN);
+        fac[0] = 2.0;
+        for (int k = 1; k < kHFacN; k++) fac[k] = 0.5 * (1.0 + std::cbrt(cfg.n_target / (double)k));
+        if (cudaMemcpy(ctx->hfac, fac.data(), sizeof(double) * kHFacN, cudaMemcpyHostToDevice) != cudaSuccess) {
+            sph_destroy(ctx);
+            return fail(nullptr, SPH_ECUDA, "copy of the h-adaptation table failed");
+        }
+    }
     int64_t zero_off[2] = {0, 0};
     sph_status s = setup_patches(ctx, 1, zero_off);
     if (s != SPH_OK) {

@@ -34,6 +34,7 @@ constexpr int kItemChunk = 4096;               // particles per work item
 constexpr int kStencilCells = 125;             // (2K+1)^3 for K <= 2
 constexpr uint32_t kFarCode = 127;             // column stencil code: offset from the cell coordinates
 constexpr int kBigShare = 64;                  // about 1/kBigShare of a patch is big
+constexpr int kHFacN = 4096;                   // entries of the h-adaptation factor table
 
 // status word bits (device, sticky until the host clears it)
 constexpr int kStOverflow = 1;
@@ -252,6 +253,8 @@ struct StepArgs {
     const uint32_t* nown;
     double courant, dt_growth, dt_fixed, n_target;
     int adapt_h, mixed;
+    const double* hfac;  // [n] 0.5 (1 + cbrt(n_target / n)) for 0 < n < kHFacN, host-computed
+
     double* partials;    // [nitems][7]
     double* cons;        // [npatch][7]
     int* status;

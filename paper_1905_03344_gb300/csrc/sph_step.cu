@@ -39,16 +39,18 @@ __device__ __forceinline__ void block_sum7(double v[7], double (*sh)[8])
     __syncthreads();
 }
 
-__device__ __forceinline__ void cons_terms(double x, double y, double vx, double vy, double vz,
-                                           double m, double u, double t[7])
+// one particle's share of the conserved sums, accumulated with FMAs: M, P,
+// L_z = m (x v_y - y v_x), twice E_kin (halved once per work item), E_int
+__device__ __forceinline__ void cons_accum(double x, double y, double vx, double vy, double vz, double m,
+                                           double u, double acc[7])
 {
-    t[0] = m;
-    t[1] = m * vx;
-    t[2] = m * vy;
-    t[3] = m * vz;
-    t[4] = m * (x * vy - y * vx);
-    t[5] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
-    t[6] = m * u;
+    acc[0] += m;
+    acc[1] = fma(m, vx, acc[1]);
+    acc[2] = fma(m, vy, acc[2]);
+    acc[3] = fma(m, vz, acc[3]);
+    acc[4] = fma(m, fma(x, vy, -y * vx), acc[4]);
+    acc[5] = fma(m, fma(vx, vx, fma(vy, vy, vz * vz)), acc[5]);
+    acc[6] = fma(m, u, acc[6]);
 }
 
 // ---- min over particles of h/c, per patch ---------------------------------
@@ -152,17 +154,18 @@ __global__ void __launch_bounds__(256) k_update(StepArgs a)
             a.s.du_prev[i] = du;
             a.s.axp[i] = ax; a.s.ayp[i] = ay; a.s.azp[i] = az;
             if (a.adapt_h) {
+                // R10 factor: a table of the host's FP64 values for the usual
+                // counts, the same expression on the device beyond it
                 const uint32_t ni = a.nown[i];
                 double f;
                 if (ni == 0) f = 2.0;
-                else if (a.mixed) f = 0.5 * (1.0 + (double)cbrtf((float)(a.n_target / (double)ni)));
+                else if (ni < (uint32_t)kHFacN) f = a.hfac[ni];
                 else f = 0.5 * (1.0 + cbrt(a.n_target / (double)ni));
                 a.s.h[i] *= f;
             }
-            double t[7];
-            cons_terms(x, y, vx, vy, vz, a.s.m[i], u, t);
-            for (int q = 0; q < 7; q++) acc[q] += t[q];
+            cons_accum(x, y, vx, vy, vz, a.s.m[i], u, acc);
         }
+        acc[5] *= 0.5;
         block_sum7(acc, sh);
         if (threadIdx.x == 0)
             for (int q = 0; q < 7; q++) a.partials[(int64_t)it * 7 + q] = acc[q];
@@ -183,11 +186,9 @@ __global__ void __launch_bounds__(256) k_conserved_items(StepArgs a)
     for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const WorkItem w = a.items[it];
         double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int64_t i = w.begin + threadIdx.x; i < w.end; i += blockDim.x) {
-            double t[7];
-            cons_terms(a.s.x[i], a.s.y[i], a.s.vx[i], a.s.vy[i], a.s.vz[i], a.s.m[i], a.s.u[i], t);
-            for (int q = 0; q < 7; q++) acc[q] += t[q];
-        }
+        for (int64_t i = w.begin + threadIdx.x; i < w.end; i += blockDim.x)
+            cons_accum(a.s.x[i], a.s.y[i], a.s.vx[i], a.s.vy[i], a.s.vz[i], a.s.m[i], a.s.u[i], acc);
+        acc[5] *= 0.5;
         block_sum7(acc, sh);
         if (threadIdx.x == 0)
             for (int q = 0; q < 7; q++) a.partials[(int64_t)it * 7 + q] = acc[q];
