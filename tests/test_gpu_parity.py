@@ -176,6 +176,28 @@ def test_mixed_pair_sums_small_cells(B, orc, case, report):
                   _oracle_forces(orc, f, lz), 1e-5, report, "mixed/%s/cf1_3" % case)
 
 
+@pytest.mark.parametrize("case", sorted(FORCE_CASES))
+def test_step_density_matches(B, orc, case, report):
+    """The timestep's density and EOS against the oracle's first step, at the
+    pair-sum tolerance: the inputs of the first step are the same on both
+    sides."""
+    f = FORCE_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    n = len(f["x"])
+    sim = B.SPH(n, precision="mixed", max_pairs=cap_pairs(n), lz=lz)
+    sim.set_particles(f)
+    sim.step(1)
+    g = {k: sim.field(k) for k in ("rho", "P", "c", "nown")}
+    sim.close()
+    ref = orc.Sim(f, lz=lz)
+    ref.step(1)
+    errs = {k: normwise(g[k], ref[k]) for k in ("rho", "P", "c")}
+    report["stepdensity/%s" % case] = errs
+    assert np.array_equal(g["nown"], ref["nown"])
+    for k, v in errs.items():
+        assert v < 1e-5, (k, v)
+
+
 def _compare_state(g, o, tol, what):
     errs = {k: normwise(g[k], o[k]) for k in ("x", "y", "u", "h", "rho")}
     errs["v"] = normwise_vec([g["vx"], g["vy"], g["vz"]], [o["vx"], o["vy"], o["vz"]])
