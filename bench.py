@@ -31,9 +31,10 @@ UNIT = "pair-interactions/s"
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-# FP32 operations per pair (FMA = 2, MUFU not counted), counted by hand from
-# k_momentum_mixed and k_density_mixed (the per-line count is in the design notes)
-FLOPS_PER_PAIR_MOMENTUM = 80
+# FP32 operations per pair (FMA = 2, MUFU and min/max not counted), counted by
+# hand from k_momentum_mixed and k_density_mixed (the per-line count is in the
+# design notes)
+FLOPS_PER_PAIR_MOMENTUM = 70
 FLOPS_PER_PAIR_DENSITY = 28
 # Algorithmic bytes of the neighbour-list kernel (k_nb_thread): 4 B per list
 # entry written, and per particle the row start (8 B), length (4 B) and own

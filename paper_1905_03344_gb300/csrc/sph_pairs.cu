@@ -370,6 +370,62 @@ __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz,
     return t;
 }
 
+#ifndef SPH_MOM_PACK
+#define SPH_MOM_PACK 1                  // two pairs at once in packed FP32x2 arithmetic
+#endif
+
+// packed FP32x2 helpers (one instruction for both halves)
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
+
+struct PairTerms2 {
+    float2 ax, ay, az, du;
+};
+
+// momentum_pair for two pairs at once: the same operations, in the halves of
+// packed FP32x2 values (mj = 0 in a half makes its terms 0)
+__device__ __forceinline__ PairTerms2 momentum_pair2(float2 dx, float2 dy, float2 dz, const float4& vi,
+                                                     const float4& ti, float wi5, const float4& va,
+                                                     const float4& vb, const float4& ta, const float4& tb,
+                                                     float2 mj, const MomConst& K)
+{
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    const float2 r2e = add2(r2, p2(1e-30f));
+    const float2 r = mul2(r2, make_float2(rsqrtf(r2e.x), rsqrtf(r2e.y)));
+    const float2 qi0 = fma2(r, p2(-vi.w), p2(1.0f));
+    const float2 qi = make_float2(fmaxf(qi0.x, 0.0f), fmaxf(qi0.y, 0.0f));
+    const float2 wj = make_float2(va.w, vb.w);
+    const float2 wj2 = mul2(wj, wj);
+    const float2 aj0 = fma2(r, mul2(wj2, p2(-1.0f)), wj);
+    const float2 aj = make_float2(fmaxf(aj0.x, 0.0f), fmaxf(aj0.y, 0.0f));
+    const float2 F = fma2(p2(wi5), mul2(mul2(qi, qi), qi), mul2(wj2, mul2(mul2(aj, aj), aj)));
+    const float2 vx = sub2(p2(vi.x), make_float2(va.x, vb.x));
+    const float2 vy = sub2(p2(vi.y), make_float2(va.y, vb.y));
+    const float2 vz = sub2(p2(vi.z), make_float2(va.z, vb.z));
+    const float2 vdot = fma2(vx, dx, fma2(vy, dy, mul2(vz, dz)));
+    const float2 hs = add2(p2(ti.w), make_float2(ta.w, tb.w));
+    const float2 den = fma2(mul2(p2(K.eps4), hs), hs, r2);
+    const float2 num = mul2(hs, vdot);
+    const float2 m2 = mul2(num, make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y)));
+    const float2 cs = add2(p2(ti.z), make_float2(ta.z, tb.z));
+    const float2 rs = add2(p2(ti.x), make_float2(ta.x, tb.x));
+    const float2 pn = mul2(m2, fma2(p2(K.beta2), m2, mul2(p2(-K.alpha2), cs)));
+    const float2 pv = mul2(pn, make_float2(__fdividef(1.0f, rs.x), __fdividef(1.0f, rs.y)));
+    const float2 pi_ = make_float2(vdot.x < 0.0f ? pv.x : 0.0f, vdot.y < 0.0f ? pv.y : 0.0f);
+    const float2 g = mul2(mj, F);
+    const float2 fa = mul2(g, add2(add2(p2(ti.y), make_float2(ta.y, tb.y)), pi_));
+    PairTerms2 t;
+    t.ax = mul2(fa, dx);
+    t.ay = mul2(fa, dy);
+    t.az = mul2(fa, dz);
+    t.du = mul2(mul2(g, p2(-1.0f)), mul2(fma2(p2(0.5f), pi_, p2(ti.y)), vdot));
+    return t;
+}
+
 struct MomAcc {
     float sx, cx, sy, cy, sz, cz, su, cu;
 };
@@ -397,6 +453,36 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         const uint32_t cws[4] = {w.x, w.y, w.z, w.w};
         const uint32_t base = ch * 4u;
         float bx = 0.0f, by = 0.0f, bz = 0.0f, bu = 0.0f;
+#if SPH_MOM_PACK
+        float2 px = p2(0.0f), py = p2(0.0f), pz = p2(0.0f), pu = p2(0.0f);
+#pragma unroll
+        for (int hh = 0; hh < 2; hh++) {
+            const uint32_t ua = base + 2u * hh;
+            if (ua >= len) break;
+            const bool hb = ua + 1u < len;
+            const uint32_t cwa = cws[2 * hh], cwb = hb ? cws[2 * hh + 1] : cwa;
+            const uint32_t ja = cwa & kColMask, jb = cwb & kColMask;
+            const float4 qa = a.r.r5[ja], qb = a.r.r5[jb];
+            const float4 va = a.r.rv[ja], vb = a.r.rv[jb];
+            const float4 ta = a.r.rt[ja], tb = a.r.rt[jb];
+            float dxa, dya, dza, dxb, dyb, dzb;
+            const uint32_t ca = cwa >> kColBits, cb = cwb >> kColBits;
+            if (ca != kFarCode) rel_dx<ZW>(tab[ca], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, qa, dxa, dya, dza);
+            else rel_dx_far(ci, a.cellxyz[ja], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, qa, dxa, dya, dza);
+            if (cb != kFarCode) rel_dx<ZW>(tab[cb], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, qb, dxb, dyb, dzb);
+            else rel_dx_far(ci, a.cellxyz[jb], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, qb, dxb, dyb, dzb);
+            const PairTerms2 t = momentum_pair2(make_float2(dxa, dxb), make_float2(dya, dyb), make_float2(dza, dzb),
+                                                vi, ti, wi5, va, vb, ta, tb, make_float2(qa.w, hb ? qb.w : 0.0f), K);
+            px = add2(px, t.ax);
+            py = add2(py, t.ay);
+            pz = add2(pz, t.az);
+            pu = add2(pu, t.du);
+        }
+        bx = px.x + px.y;
+        by = py.x + py.y;
+        bz = pz.x + pz.y;
+        bu = pu.x + pu.y;
+#else
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             if (base + (uint32_t)u >= len) break;
@@ -417,6 +503,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
             bz += t.az;
             bu += t.du;
         }
+#endif
         kahan_add(A.sx, A.cx, bx);
         kahan_add(A.sy, A.cy, by);
         kahan_add(A.sz, A.cz, bz);
@@ -446,7 +533,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
 }
 
 #ifndef SPH_MOM_MINB
-#define SPH_MOM_MINB 3                  // resident 256-thread CTAs per SM the registers are sized for
+#define SPH_MOM_MINB 2                  // resident 256-thread CTAs per SM the registers are sized for
 #endif
 template <int TPP>
 __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a)
