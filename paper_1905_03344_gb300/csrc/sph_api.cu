@@ -632,7 +632,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ok = ok && dalloc(ctx, cellrec, (size_t)ctx->cap_cells) && dalloc(ctx, cellxyz, N);
     ctx->grid.cell = cellrec;
     ctx->grid.cellxyz = cellxyz;
-    ok = ok && dalloc(ctx, ctx->rec.r4, N);
+    // kGroup-style padding: the list search reads groups of records past a cell
+    ok = ok && dalloc(ctx, ctx->rec.r4, N + 16);
     if (ctx->mixed) {
         ok = ok && dalloc(ctx, ctx->rec.r5, N) && dalloc(ctx, ctx->rec.rv, N) && dalloc(ctx, ctx->rec.rt, N) &&
              dalloc(ctx, ctx->rec.hc, N) && dalloc(ctx, ctx->rec.pf, N) && dalloc(ctx, ctx->rec.uf, N) &&

@@ -66,7 +66,7 @@ __device__ __noinline__ int exact_pair_at(const NbArgs& a, int64_t i, uint32_t j
 }
 
 #ifndef SPH_NB_MINB
-#define SPH_NB_MINB 7                   // resident CTAs per SM the registers are sized for
+#define SPH_NB_MINB 8                   // resident CTAs per SM the registers are sized for
 #endif
 #ifndef SPH_NB_GROUP
 #define SPH_NB_GROUP 4                  // candidates loaded together per lane
@@ -185,6 +185,7 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
     const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f, inv_lz = 1.0f / P->lz_f;
     const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
     const uint32_t cbase = (uint32_t)P->cell_base;
+    const uint32_t i32 = (uint32_t)i;
     const float4 ri = a.r4[i];
     const uint32_t cc = a.g.cellxyz[i];
     const int cx = cc & 255, cy = (cc >> 8) & 255, cz = cc >> 16;
@@ -254,11 +255,15 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
                 // offsets of up to 2 cells have a stencil code; K = 3 reaches 3
                 const uint32_t kk = (K <= 2 ? kkrow + (uint32_t)dcx
                                             : stencil_code(P, dcx, dcy, ZW ? zd : zd - 2, !ZW)) << kColBits;
-                // kGroup candidates per iteration: their gathers are in flight together
+                // kGroup candidates per iteration: their gathers are in flight
+                // together (the record array has kGroup padding entries, so a
+                // group may read past the cell; those slots are masked)
                 for (uint32_t jb = se.x; jb < se.y; jb += kGroup) {
+                    const float4* qp = a.r4 + jb;
                     float4 q[kGroup];
 #pragma unroll
-                    for (int u = 0; u < kGroup; u++) q[u] = a.r4[min(jb + (uint32_t)u, se.y - 1u)];
+                    for (int u = 0; u < kGroup; u++) q[u] = qp[u];
+                    const uint32_t rem = se.y - jb;
                     float r2[kGroup], T[kGroup];
                     unsigned near = 0;
 #pragma unroll
@@ -268,7 +273,7 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
                         if (ZW) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
                         r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         T[u] = fmaxf(Ti, q[u].w);
-                        if (jb + (uint32_t)u < se.y && r2[u] <= T[u] * fhi) near |= 1u << u;
+                        if ((uint32_t)u < rem && r2[u] <= T[u] * fhi) near |= 1u << u;
                     }
                     if (!near) continue;
                     const uint32_t c0 = row.cnt;
@@ -276,7 +281,7 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
                     for (int u = 0; u < kGroup; u++) {
                         if (!(near & (1u << u))) continue;
                         const uint32_t j = jb + (uint32_t)u;
-                        if ((int64_t)j == i) continue;
+                        if (j == i32) continue;
                         row_decide<MODE>(a, P, i, j, r2[u], Ti, T[u], flo, fhi, j | kk, row);
                     }
                     row_group_end<MODE>(row, c0);
