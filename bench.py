@@ -36,6 +36,10 @@ SM_MAX_MHZ = 2070.0
 # design notes)
 FLOPS_PER_PAIR_MOMENTUM = 70
 FLOPS_PER_PAIR_DENSITY = 28
+# FP64 operations per pair of k_momentum_fp64 (mul/add each 1, sqrt and
+# divisions not counted): 47 on every pair plus 17 for the viscosity of
+# approaching pairs, taken on half of them
+FLOPS_PER_PAIR_MOMENTUM_FP64 = 56
 # Algorithmic bytes of the neighbour-list kernel (k_nb_thread): 4 B per list
 # entry written, and per particle the row start (8 B), length (4 B) and own
 # count (4 B) written plus its record (16 B), h (8 B), cell (4 B) and row hint
@@ -119,6 +123,23 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def cpu_baseline_1thread(sample_n=40, nsteps=1):
+    """The same oracle step on one host core, on the 40^3 patch."""
+    import oracle
+    from paper_1905_03344_gb300 import inputs
+    f = inputs.square_patch(sample_n)
+    sim = oracle.Sim(f, nthreads=1)
+    t0 = time.perf_counter()
+    pairs = 0
+    for _ in range(nsteps):
+        sim.step(1)
+        pairs += sim.nnz
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d full oracle step(s) on the %d^3 square patch (%d particles), one host core; %.1f s"
+                      % (nsteps, sample_n, sample_n ** 3, dt)}
+
+
 def cpu_baseline(sample_n=100, nsteps=1):
     """The FP64 oracle (as it stands) on host cores, one full step on the
     100^3 patch: the same rotating-patch workload at 1/8 of the particles."""
@@ -179,7 +200,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
@@ -367,6 +388,20 @@ def main():
         p64 = s64.pair_count(reset=True) / args.fp64_steps
         line["fp64_path"] = {"value": 2.0 * p64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                              "steps_per_s": 1e3 / ms64, "steps": args.fp64_steps}
+        # the FP64 path's momentum sum against the FP64 FMA rate
+        s64.profile(True)
+        s64.profile()
+        s64.step(1)
+        torch.cuda.synchronize()
+        prof64 = s64.profile()
+        s64.profile(False)
+        fma64 = binding.sph_fma_peak("fp64", stream=stream.cuda_stream) / 1e12
+        mom64_ms = prof64["momentum"][0]
+        mom64_tf = FLOPS_PER_PAIR_MOMENTUM_FP64 * p64 / (mom64_ms / 1e3) / 1e12
+        line["fp64_path"]["roofline_pair_sum"] = {
+            "bound": "alu", "kernel": "k_momentum_fp64", "achieved": mom64_tf, "peak": fma64, "unit": "TFLOP/s",
+            "frac": mom64_tf / fma64, "peak_source": "measured: sph_fma_peak FP64 FMA chains",
+            "flops_per_pair": FLOPS_PER_PAIR_MOMENTUM_FP64, "ms_per_launch": mom64_ms}
         line["mixed_over_fp64"] = line["ms_per_step"] and ms64 / line["ms_per_step"]
         s64.close()
         sim = make(args.precision)
@@ -395,6 +430,12 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline_1core"] = cpu_baseline_1thread()
+        try:
+            cpu = [l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo") if l.lower().startswith(("model name", "cpu part"))]
+        except OSError:
+            cpu = []
+        line["cpu_baseline"]["host"] = {"nproc": os.cpu_count(), "cpu": cpu[0] if cpu else "unknown"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -33,7 +33,10 @@ constexpr int kMaxPatches = 256;
 constexpr int kItemChunk = 4096;               // particles per work item
 constexpr int kStencilCells = 125;             // (2K+1)^3 for K <= 2
 constexpr uint32_t kFarCode = 127;             // column stencil code: offset from the cell coordinates
-constexpr int kBigShare = 64;                  // about 1/kBigShare of a patch is big
+#ifndef SPH_BIG_SHARE
+#define SPH_BIG_SHARE 64
+#endif
+constexpr int kBigShare = SPH_BIG_SHARE;       // about 1/kBigShare of a patch is big
 constexpr int kHFacN = 4096;                   // entries of the h-adaptation factor table
 
 // status word bits (device, sticky until the host clears it)
