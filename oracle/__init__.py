@@ -72,6 +72,11 @@ def lib():
         L.orc_conserved.argtypes = [ctypes.c_int64] + [_D] * 8
         L.orc_step.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcState), ctypes.c_int]
+        L.orc_set_kernel.restype = ctypes.c_int
+        L.orc_set_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_sinc_bn.restype = ctypes.c_double
+        L.orc_sinc_bn.argtypes = [ctypes.c_int]
+        L.orc_kernel_bn.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -86,6 +91,36 @@ def _f64(a):
 
 def sigma_w():
     return lib().orc_sigma_w()
+
+
+KERNELS = {"wendland": 0, "sinc": 1}
+
+
+def set_kernel(kind="wendland", n=6):
+    """Selects the kernel of every later call: "wendland" (Eq. 2) or "sinc"
+    with index n (the Sinc family of Sec. 3)."""
+    if lib().orc_set_kernel(KERNELS[kind], int(n)) != 0:
+        raise ValueError("unsupported kernel %s/%d" % (kind, n))
+
+
+class kernel:
+    """with oracle.kernel("sinc", 6): ... -- the kernel for the block, then Wendland."""
+
+    def __init__(self, kind="wendland", n=6):
+        self.kind, self.n = kind, n
+
+    def __enter__(self):
+        set_kernel(self.kind, self.n)
+        return self
+
+    def __exit__(self, *exc):
+        set_kernel("wendland")
+        return False
+
+
+def sinc_bn(n):
+    """B_n of the Sinc kernel (normalisation by composite Simpson)."""
+    return lib().orc_sinc_bn(int(n))
 
 
 def w(r, h):
@@ -185,7 +220,7 @@ class Sim:
 
     def __init__(self, fields, gamma=5.0 / 3.0, n_target=100.0, courant=0.2, dt_growth=1.1,
                  av_alpha=1.0, av_beta=2.0, av_eps=0.01, lz=1.0, adapt_h=True, dt_fixed=0.0,
-                 use_grid=-1, nthreads=1):
+                 use_grid=-1, nthreads=1, kernel="wendland", kernel_n=6):
         n = len(fields["x"])
         self.n = n
         self.arr = {}
@@ -209,12 +244,14 @@ class Sim:
         self.st.dt_prev = 0.0
         self.st.step = 0
         self.nthreads = nthreads
+        self.kernel = (kernel, kernel_n)
 
     def step(self, nsteps=1):
-        for _ in range(nsteps):
-            r = lib().orc_step(ctypes.byref(self.params), ctypes.byref(self.st), self.nthreads)
-            if r != 0:
-                raise RuntimeError("oracle step failed")
+        with kernel(*self.kernel):
+            for _ in range(nsteps):
+                r = lib().orc_step(ctypes.byref(self.params), ctypes.byref(self.st), self.nthreads)
+                if r != 0:
+                    raise RuntimeError("oracle step failed")
         return self
 
     def __getitem__(self, k):

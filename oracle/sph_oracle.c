@@ -14,7 +14,8 @@
  * neighbour predicate below is evaluated exactly in the order written.
  *
  * What each function follows:
- *   orc_w, orc_gradw_fac ...... Eq. 2 (Wendland kernel, Sec. 3), 1/h^3 restored
+ *   orc_w, orc_gradw_fac ...... Eq. 2 (Wendland kernel, Sec. 3), 1/h^3 restored,
+ *                               or the Sinc family of Sec. 3 (orc_set_kernel)
  *   orc_pair_in ............... neighbour predicate, symmetric union (R11)
  *   orc_neighbors_brute ....... O(N^2) definition of the neighbour set (Table 1
  *                               "Neighbour Discovery"; the tree walk is replaced
@@ -54,8 +55,103 @@
 /* ------------------------------------------------------------------------ */
 double orc_sigma_w(void) { return 21.0 / (16.0 * M_PI); }
 
+/* ------------------------------------------------------------------------ */
+/* Kernel family.  Sec. 3 gives the mini-app two kernels: Wendland (Eq. 2)    */
+/* and the Sinc functions                                                    */
+/*   W_n(v, h) = B_n / h^3 S_n(pi v / 2),  0 <= v <= 2,  S_n = sinc^n,          */
+/*   sinc(x) = sin(x) / x,                                                   */
+/* B_n the normalisation: int W d^3x = 1, i.e.                               */
+/*   4 pi B_n int_0^2 v^2 S_n(pi v / 2) dv = 1,                               */
+/* evaluated here by composite Simpson's rule.                               */
+/* ------------------------------------------------------------------------ */
+enum { ORC_WENDLAND = 0, ORC_SINC = 1 };
+static int g_kernel = ORC_WENDLAND;
+static int g_sinc_n = 6;
+static double g_sinc_bn = 0.0;
+
+static double sinc_of(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
+
+static double ipow(double b, int e)
+{
+    double r = 1.0;
+    for (int k = 0; k < e; k++) r *= b;
+    return r;
+}
+
+double orc_sinc_bn(int n)
+{
+    const int M = 200000; /* even number of Simpson intervals on [0, 2] */
+    const double dv = 2.0 / M;
+    double s = 0.0;
+    for (int k = 0; k <= M; k++) {
+        double v = k * dv;
+        double f = v * v * ipow(sinc_of(0.5 * M_PI * v), n);
+        double wgt = (k == 0 || k == M) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+        s += wgt * f;
+    }
+    s *= dv / 3.0;
+    return 1.0 / (4.0 * M_PI * s);
+}
+
+/* kind 0: Wendland (Eq. 2); kind 1: Sinc with index n (n >= 2) */
+int orc_set_kernel(int kind, int n)
+{
+    if (kind == ORC_WENDLAND) {
+        g_kernel = ORC_WENDLAND;
+        return 0;
+    }
+    if (kind == ORC_SINC && n >= 2 && n <= 16) {
+        g_kernel = ORC_SINC;
+        g_sinc_n = n;
+        g_sinc_bn = orc_sinc_bn(n);
+        return 0;
+    }
+    return -1;
+}
+
+double orc_kernel_bn(void) { return g_kernel == ORC_SINC ? g_sinc_bn : orc_sigma_w(); }
+
+/* (sin x - x cos x) / x^3: by its Taylor series sum_{m>=1} (-1)^(m+1) 2m
+ * x^(2m-2) / (2m+1)! below x = 1 (the direct form cancels there), directly
+ * above */
+static double sinc_slope(double x)
+{
+    if (x < 1.0) {
+        double x2 = x * x, t = 0.0, pw = 1.0, fact = 6.0; /* (2m+1)! for m = 1 */
+        for (int m = 1; m <= 10; m++) {
+            double term = 2.0 * m * pw / fact;
+            t += (m & 1) ? term : -term;
+            pw *= x2;
+            fact *= (2.0 * m + 2.0) * (2.0 * m + 3.0);
+        }
+        return t;
+    }
+    return (sin(x) - x * cos(x)) / (x * x * x);
+}
+
+static double w_sinc(double r, double h)
+{
+    double v = r / h;
+    if (v >= 2.0) return 0.0;
+    return g_sinc_bn / (h * h * h) * ipow(sinc_of(0.5 * M_PI * v), g_sinc_n);
+}
+
+/* dW/dr = B_n/h^3 n S^(n-1) sinc'(x) dx/dr with x = pi v/2, dx/dr = pi/(2h);
+ * sinc'(x) = -(sin x - x cos x)/x^2 and r = 2 h x / pi, so with
+ * grad_i W = -f (x_i - x_j):  f = B_n n pi^2 / (4 h^5) S^(n-1) (sin x - x cos x)/x^3 */
+static double gradw_fac_sinc(double r, double h)
+{
+    double v = r / h;
+    if (v >= 2.0) return 0.0;
+    double x = 0.5 * M_PI * v;
+    double h2 = h * h;
+    return g_sinc_bn * g_sinc_n * M_PI * M_PI / (4.0 * h2 * h2 * h) * ipow(sinc_of(x), g_sinc_n - 1) *
+           sinc_slope(x);
+}
+
 double orc_w(double r, double h)
 {
+    if (g_kernel == ORC_SINC) return w_sinc(r, h);
     double v = r / h;
     if (v >= 2.0) return 0.0;
     double q = 1.0 - 0.5 * v;
@@ -67,6 +163,7 @@ double orc_w(double r, double h)
  * Returns the scalar f >= 0 with grad_i W = -f * (x_i - x_j).                */
 double orc_gradw_fac(double r, double h)
 {
+    if (g_kernel == ORC_SINC) return gradw_fac_sinc(r, h);
     double v = r / h;
     if (v >= 2.0) return 0.0;
     double q = 1.0 - 0.5 * v;
