@@ -54,7 +54,7 @@ typedef enum {
 } sph_status;
 
 enum { SPH_FP64 = 0, SPH_MIXED = 1 };               /* sph_config.precision */
-enum { SPH_KERNEL_WENDLAND = 0 };                   /* sph_config.kernel */
+enum { SPH_KERNEL_WENDLAND = 0, SPH_KERNEL_SINC = 1 }; /* sph_config.kernel */
 
 /* Fields for sph_get_field (all returned as double, original order). */
 enum {
@@ -72,7 +72,10 @@ enum {
 
 typedef struct {
     int32_t precision;      /* SPH_FP64 or SPH_MIXED (FP32 pair sums, Kahan) */
-    int32_t kernel;         /* SPH_KERNEL_WENDLAND (Eq. 2) */
+    int32_t kernel;         /* SPH_KERNEL_WENDLAND (Eq. 2, the default) or
+                               SPH_KERNEL_SINC: W = B_n / h^3 sinc^n(pi v / 2),
+                               0 <= v <= 2 (Sec. 3), B_n normalising it */
+    int32_t kernel_n;       /* n of the Sinc kernel, 2..16 (default 6) */
     double gamma;           /* ideal-gas exponent, 5/3 */
     double n_target;        /* target neighbour count of h adaptation, 100 */
     double courant;         /* Courant factor C, 0.2 */

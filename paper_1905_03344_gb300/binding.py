@@ -18,7 +18,7 @@ from . import build as _build
 
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EOVERFLOW, SPH_ENONFINITE, SPH_ETIMEOUT, SPH_ESTATE = range(8)
 SPH_FP64, SPH_MIXED = 0, 1
-SPH_KERNEL_WENDLAND = 0
+SPH_KERNEL_WENDLAND, SPH_KERNEL_SINC = 0, 1
 
 FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "h", "u", "du_prev", "axp", "ayp", "azp",
           "rho", "P", "c", "ax", "ay", "az", "du", "nown", "nnb"]
@@ -27,7 +27,7 @@ PHASES = ["bbox", "keys", "sort", "gather", "nb_reset", "nb", "density", "moment
 
 
 class SphConfig(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("kernel", ctypes.c_int32),
+    _fields_ = [("precision", ctypes.c_int32), ("kernel", ctypes.c_int32), ("kernel_n", ctypes.c_int32),
                 ("gamma", ctypes.c_double), ("n_target", ctypes.c_double),
                 ("courant", ctypes.c_double), ("dt_growth", ctypes.c_double),
                 ("av_alpha", ctypes.c_double), ("av_beta", ctypes.c_double),
@@ -341,6 +341,8 @@ class SPH:
     def __init__(self, max_particles, precision="mixed", max_patches=1, stream=None, **kw):
         cfg = sph_config_default()
         cfg.precision = SPH_FP64 if precision == "fp64" else SPH_MIXED
+        if isinstance(kw.get("kernel"), str):
+            kw["kernel"] = {"wendland": SPH_KERNEL_WENDLAND, "sinc": SPH_KERNEL_SINC}[kw["kernel"]]
         cfg.max_particles = int(max_particles)
         cfg.max_patches = int(max_patches)
         if stream is not None:

@@ -99,6 +99,7 @@ struct sph_ctx {
     WorkItem* items = nullptr;
     double *partials = nullptr, *cons = nullptr, *scratch = nullptr;
     double* hfac = nullptr;        // h-adaptation factors by neighbour count
+    double kernel_b = 0.0;         // sigma_W (Wendland) or B_n (Sinc)
     int* status = nullptr;
     int* h_status = nullptr;     // pinned
     unsigned long long* pair_acc = nullptr;  // sum of |N| over the steps taken
@@ -223,6 +224,34 @@ void collect_profile(sph_ctx* ctx)
     ctx->marks.clear();
 }
 
+// ---- kernel normalisation -------------------------------------------------------
+// Wendland (Eq. 2): sigma_W = 21 / (16 pi).  Sinc (Sec. 3): B_n from
+// 4 pi B_n int_0^2 v^2 sinc^n(pi v / 2) dv = 1, the integral by composite
+// 5-point Gauss-Legendre quadrature on 400 panels (the integrand is smooth).
+double kernel_norm(int kernel, int n)
+{
+    const double pi = 3.14159265358979323846;
+    if (kernel != SPH_KERNEL_SINC) return 21.0 / (16.0 * pi);
+    const double xg[5] = {0.0, -0.5384693101056831, 0.5384693101056831, -0.9061798459386640, 0.9061798459386640};
+    const double wg[5] = {0.5688888888888889, 0.4786286704993665, 0.4786286704993665, 0.2369268850561891,
+                          0.2369268850561891};
+    const int panels = 400;
+    const double hw = 1.0 / panels;  // half width of a panel on [0, 2]
+    double total = 0.0;
+    for (int p = 0; p < panels; p++) {
+        const double mid = (2.0 * p + 1.0) * hw;
+        for (int k = 0; k < 5; k++) {
+            const double v = mid + hw * xg[k];
+            const double x = 0.5 * pi * v;
+            const double s = x == 0.0 ? 1.0 : std::sin(x) / x;
+            double sn = 1.0;
+            for (int e = 0; e < n; e++) sn *= s;
+            total += wg[k] * hw * v * v * sn;
+        }
+    }
+    return 1.0 / (4.0 * pi * total);
+}
+
 // ---- argument bundles ---------------------------------------------------------
 NbArgs nb_args(sph_ctx* ctx)
 {
@@ -264,6 +293,9 @@ PairArgs pair_args(sph_ctx* ctx)
     a.alpha = ctx->cfg.av_alpha;
     a.beta = ctx->cfg.av_beta;
     a.eps = ctx->cfg.av_eps;
+    a.kernel = ctx->cfg.kernel;
+    a.kernel_n = ctx->cfg.kernel_n;
+    a.kb = ctx->kernel_b;
     a.status = ctx->status;
     return a;
 }
@@ -496,6 +528,7 @@ void sph_config_default(sph_config* c)
     memset(c, 0, sizeof(*c));
     c->precision = SPH_MIXED;
     c->kernel = SPH_KERNEL_WENDLAND;
+    c->kernel_n = 6;
     c->gamma = 5.0 / 3.0;
     c->n_target = 100.0;
     c->courant = 0.2;
@@ -562,7 +595,10 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     else sph_config_default(&cfg);
     if (cfg.precision != SPH_FP64 && cfg.precision != SPH_MIXED)
         return fail(nullptr, SPH_EINVAL, "precision must be SPH_FP64 or SPH_MIXED");
-    if (cfg.kernel != SPH_KERNEL_WENDLAND) return fail(nullptr, SPH_EINVAL, "unsupported kernel");
+    if (cfg.kernel != SPH_KERNEL_WENDLAND && cfg.kernel != SPH_KERNEL_SINC)
+        return fail(nullptr, SPH_EINVAL, "unsupported kernel");
+    if (cfg.kernel == SPH_KERNEL_SINC && !(cfg.kernel_n >= 2 && cfg.kernel_n <= 16))
+        return fail(nullptr, SPH_EINVAL, "kernel_n must be in [2, 16] for the Sinc kernel");
     if (cfg.max_particles < 1 || cfg.max_particles > kMaxParticles)
         return fail(nullptr, SPH_EINVAL, "max_particles must be in [1, 2^25]");
     if (cfg.max_patches < 1 || cfg.max_patches > kMaxPatches)
@@ -601,6 +637,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         ctx->own_stream = true;
     }
     ctx->mixed = cfg.precision == SPH_MIXED;
+    ctx->kernel_b = kernel_norm(cfg.kernel, cfg.kernel_n);
     ctx->cell_factor = cfg.cell_factor;
     if (t) ctx->tpp_pair = t;
     ctx->cap_n = cfg.max_particles;

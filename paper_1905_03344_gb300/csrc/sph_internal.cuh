@@ -238,6 +238,8 @@ struct PairArgs {
     Recs r;
     Fp64 f;
     double gamma, alpha, beta, eps;
+    int kernel, kernel_n;                // SPH_KERNEL_*; n of the Sinc kernel
+    double kb;                           // sigma_W (Wendland) or B_n (Sinc)
     int* status;
 };
 int launch_density(const Launch& L, const PairArgs& a, int tpp, int mixed);

@@ -25,9 +25,6 @@
 
 namespace sphg {
 
-constexpr double kSigmaW = 21.0 / (16.0 * 3.14159265358979323846);
-constexpr float kSigmaWf = (float)kSigmaW;
-constexpr float k80Sigma = (float)(80.0 * kSigmaW);
 
 #ifndef SPH_MOM_CHUNK
 #define SPH_MOM_CHUNK 1                 // momentum: row words in chunks of four (below)
@@ -139,6 +136,131 @@ __device__ __forceinline__ void rel_dx(const float4& e, float s_f, float sz_f, f
     }
 }
 
+// ---------------------------------------------------------------------------
+// The two kernels of Sec. 3, with w = 1/(2h):
+//   Wendland (Eq. 2): W = sigma/h^3 q^4 (5 - 4q), q = 1 - r w;
+//     grad_i W = -160 sigma w^5 q^3 (x_i - x_j)
+//   Sinc: W = B_n/h^3 S^n, S = sin(x)/x, x = pi r w (= pi v / 2);
+//     grad_i W = -8 B_n n pi^2 w^5 S^(n-1) g(x) (x_i - x_j), g = (sin x - x cos x)/x^3
+// The pair loops carry only the factors that depend on r (the density
+// weight, and w^5 times the shape of the gradient); the constants are
+// applied once per particle: rho = 8 kb w_i^3 (sum + m_i), and grad_i Wbar
+// is half the two sides' gradients, 80 sigma or 4 B_n n pi^2 times the sum
+// of the two sides' factors (kb = sigma or B_n).
+// ---------------------------------------------------------------------------
+constexpr float kPif = 3.14159265358979323846f;
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ float ipowf(float b, int e)
+{
+    float r = 1.0f;
+    for (int k = 0; k < e; k++) r *= b;
+    return r;
+}
+__device__ __forceinline__ double ipowd(double b, int e)
+{
+    double r = 1.0;
+    for (int k = 0; k < e; k++) r *= b;
+    return r;
+}
+
+// g(x) = (sin x - x cos x)/x^3: its Taylor series sum_m (-1)^(m+1) 2m x^(2m-2)
+// / (2m+1)! below x = 1, where the direct form loses digits to cancellation
+__device__ __forceinline__ float sinc_g(float x, float sn, float cs)
+{
+    if (x < 1.0f) {
+        const float x2 = x * x;
+        return fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 3991680.0f, -1.0f / 45360.0f), 1.0f / 840.0f),
+                             -1.0f / 30.0f),
+                    1.0f / 3.0f);
+    }
+    return __fdividef(fmaf(-x, cs, sn), x * x * x);
+}
+__device__ __forceinline__ double sinc_g(double x, double sn, double cs)
+{
+    if (x < 1.0) {
+        const double x2 = x * x;
+        double t = 0.0, pw = 1.0, fact = 6.0;
+        for (int m = 1; m <= 10; m++) {
+            const double term = 2.0 * m * pw / fact;
+            t += (m & 1) ? term : -term;
+            pw *= x2;
+            fact *= (2.0 * m + 2.0) * (2.0 * m + 3.0);
+        }
+        return t;
+    }
+    return (sn - x * cs) / (x * x * x);
+}
+
+template <int KERN>
+struct KernF;
+
+template <>
+struct KernF<SPH_KERNEL_WENDLAND> {
+    // density weight q^4 (5 - 4q)
+    static __device__ __forceinline__ float dens(float r, float w, int)
+    {
+        const float q = fmaxf(fmaf(-r, w, 1.0f), 0.0f);
+        const float q2 = q * q;
+        return q2 * q2 * fmaf(-4.0f, q, 5.0f);
+    }
+    static __device__ __forceinline__ double dens(double r, double w, int)
+    {
+        const double q = fmax(1.0 - r * w, 0.0);
+        const double q2 = q * q;
+        return q2 * q2 * (5.0 - 4.0 * q);
+    }
+    // gradient factor w^5 q^3
+    static __device__ __forceinline__ float grad(float r, float w, float w5, int)
+    {
+        const float q = fmaxf(fmaf(-r, w, 1.0f), 0.0f);
+        return w5 * (q * q * q);
+    }
+    static __device__ __forceinline__ double grad(double r, double w, double w5, int)
+    {
+        const double q = fmax(1.0 - r * w, 0.0);
+        return w5 * q * q * q;
+    }
+    static __host__ __device__ double grad_scale(double kb, int) { return 80.0 * kb; }
+};
+
+template <>
+struct KernF<SPH_KERNEL_SINC> {
+    static __device__ __forceinline__ float dens(float r, float w, int n)
+    {
+        const float x = kPif * r * w;
+        if (!(x < kPif)) return 0.0f;
+        float sn, cs;
+        __sincosf(x, &sn, &cs);
+        return ipowf(x > 0.0f ? __fdividef(sn, x) : 1.0f, n);
+    }
+    static __device__ __forceinline__ double dens(double r, double w, int n)
+    {
+        const double x = kPi * r * w;
+        if (!(x < kPi)) return 0.0;
+        return ipowd(x > 0.0 ? sin(x) / x : 1.0, n);
+    }
+    static __device__ __forceinline__ float grad(float r, float w, float w5, int n)
+    {
+        const float x = kPif * r * w;
+        if (!(x < kPif)) return 0.0f;
+        float sn, cs;
+        __sincosf(x, &sn, &cs);
+        const float S = x > 0.0f ? __fdividef(sn, x) : 1.0f;
+        return w5 * ipowf(S, n - 1) * sinc_g(x, sn, cs);
+    }
+    static __device__ __forceinline__ double grad(double r, double w, double w5, int n)
+    {
+        const double x = kPi * r * w;
+        if (!(x < kPi)) return 0.0;
+        double sn, cs;
+        sincos(x, &sn, &cs);
+        const double S = x > 0.0 ? sn / x : 1.0;
+        return w5 * ipowd(S, n - 1) * sinc_g(x, sn, cs);
+    }
+    static __host__ __device__ double grad_scale(double kb, int n) { return 4.0 * kb * n * kPi * kPi; }
+};
+
 // The list words stream from HBM (the pool is far larger than L2).  Each
 // group asks L2 for the row of the particle it takes next -- the group's lanes
 // cover it in 128-byte lines -- while it works on the current one; the start
@@ -170,12 +292,13 @@ __device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowA
 // ---------------------------------------------------------------------------
 // A5 + A6, mixed precision
 // ---------------------------------------------------------------------------
-// the row of one particle: plain FP32 weights m_j q^4 (5 - 4q), Kahan sum
-template <int TPP, int ZW>
+// the row of one particle: plain FP32 weights m_j W-shape(r), Kahan sum
+template <int TPP, int ZW, int KERN>
 __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                             int gl, float s_f, float sz_f, float lz_f, const float4& ri, float inv2h,
                                             uint32_t ci, float& sum, float& comp)
 {
+    const int kn = a.kernel_n;
 #if SPH_DEN_CHUNK
     // chunks of four row words as in the momentum sum
     const uint4* row4 = reinterpret_cast<const uint4*>(row);
@@ -203,10 +326,8 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
                 rel_dx_far(ci, a.cellxyz[cw[u] & kColMask], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float r = r2 * rsqrtf(r2 + 1e-30f);
-            const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
-            const float q2 = qv * qv;
             const float m = base + (uint32_t)u < len ? q[u].w : 0.0f;
-            b = fmaf(m, q2 * q2 * fmaf(-4.0f, qv, 5.0f), b);
+            b = fmaf(m, KernF<KERN>::dens(r, inv2h, kn), b);
         }
         kahan_add(sum, comp, b);
     }
@@ -229,18 +350,17 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
                 rel_dx_far(ci, a.cellxyz[cw[u] & kColMask], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q[u], dx, dy, dz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float r = r2 * rsqrtf(r2 + 1e-30f);
-            const float qv = fmaxf(fmaf(-r, inv2h, 1.0f), 0.0f);
-            const float q2 = qv * qv;
             const float m = k + (uint32_t)(u * TPP) < len ? q[u].w : 0.0f;
-            kahan_fma(sum, comp, m, q2 * q2 * fmaf(-4.0f, qv, 5.0f));
+            kahan_fma(sum, comp, m, KernF<KERN>::dens(r, inv2h, kn));
         }
     }
 #endif
 }
 
-template <int TPP>
+template <int TPP, int KERN>
 __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 {
+    const float kb8 = (float)(8.0 * a.kb);
     __shared__ float4 tab[kStencilCells];
     fill_stencil_table(tab);
     if (*a.status & kStBad) return;
@@ -260,12 +380,12 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
         const uint32_t len = a.cnt[i];
         const uint32_t ci = a.cellxyz[i];
         float sum = 0.0f, comp = 0.0f;
-        if (P->zmode) density_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
-        else density_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
+        if (P->zmode) density_row<TPP, 1, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
+        else density_row<TPP, 0, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
         group_kahan_reduce<TPP>(sum, comp, G.gmask);
         if (G.gl == 0) {
             const float tot = ri.w + (sum - comp);           // self term m_i W(0) ~ m_i
-            const float rho = kSigmaWf * tot * (8.0f * inv2h * inv2h * inv2h);
+            const float rho = kb8 * tot * (inv2h * inv2h * inv2h);
             const float u = a.r.uf[i];                       // specific energy, staged by the gather
             const float Pr = (gam - 1.0f) * rho * u;
             const float c = sqrtf(gam * Pr / rho);
@@ -283,9 +403,10 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 // ---------------------------------------------------------------------------
 // A5 + A6, FP64
 // ---------------------------------------------------------------------------
-template <int TPP>
+template <int TPP, int KERN>
 __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
 {
+    const int kn = a.kernel_n;
     if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
@@ -304,13 +425,11 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
             if (dz > hl) dz -= lz;
             else if (dz < -hl) dz += lz;
             const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            const double qv = fmax(1.0 - r * w, 0.0);
-            const double q2 = qv * qv;
-            sum += a.s.m[j] * (q2 * q2 * (5.0 - 4.0 * qv));
+            sum += a.s.m[j] * KernF<KERN>::dens(r, w, kn);
         }
         sum = group_sum<TPP>(sum, G.gmask);
         if (G.gl == 0) {
-            const double rho = kSigmaW * (a.s.m[i] + sum) / (hi * hi * hi);
+            const double rho = a.kb * (a.s.m[i] + sum) / (hi * hi * hi);
             const double Pr = (a.gamma - 1.0) * rho * a.s.u[i];
             const double c = sqrt(a.gamma * Pr / rho);
             a.f.rho[i] = rho;
@@ -342,17 +461,24 @@ struct MomConst {
 };
 
 // one pair of the momentum and energy sums, from x_i - x_j = (dx, dy, dz);
-// w^5 q^3 = w^2 (w q)^3 with w q = w - r w^2
+// Wendland: w^5 q^3 = w^2 (w q)^3 with w q = w - r w^2
+template <int KERN>
 __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz, const float4& vi,
                                                    const float4& ti, float wi5, const float4& vj,
-                                                   const float4& tj, float mj, const MomConst& K)
+                                                   const float4& tj, float mj, const MomConst& K, int kn)
 {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
-    const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
-    const float wj2 = vj.w * vj.w;
-    const float aj = fmaxf(fmaf(-r, wj2, vj.w), 0.0f);          // w_j q_j
-    const float F = fmaf(wi5, qi * qi * qi, wj2 * (aj * aj * aj));
+    float F;
+    if (KERN == SPH_KERNEL_WENDLAND) {
+        const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
+        const float wj2 = vj.w * vj.w;
+        const float aj = fmaxf(fmaf(-r, wj2, vj.w), 0.0f);      // w_j q_j
+        F = fmaf(wi5, qi * qi * qi, wj2 * (aj * aj * aj));
+    } else {
+        const float wj2 = vj.w * vj.w;
+        F = KernF<KERN>::grad(r, vi.w, wi5, kn) + KernF<KERN>::grad(r, vj.w, wj2 * wj2 * vj.w, kn);
+    }
     const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const float vdot = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
     const float hs = ti.w + tj.w;
@@ -437,12 +563,13 @@ struct MomAcc {
 // sums the chunk's four pair terms plainly and adds that sum with Kahan
 // compensation (the plain sum of four terms errs by at most 3 eps times their
 // magnitudes, the order of one term's own rounding).
-template <int TPP, int ZW>
+template <int TPP, int ZW, int KERN>
 __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                              int gl, float s_f, float sz_f, float lz_f, const float4& ri,
                                              const float4& vi, const float4& ti, float wi5, const MomConst& K,
                                              uint32_t ci, MomAcc& A)
 {
+    const int kn = a.kernel_n;
 #if SPH_MOM_CHUNK
     const uint4* row4 = reinterpret_cast<const uint4*>(row);
     const uint32_t nch = (len + 3u) >> 2;
@@ -454,6 +581,8 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         const uint32_t base = ch * 4u;
         float bx = 0.0f, by = 0.0f, bz = 0.0f, bu = 0.0f;
 #if SPH_MOM_PACK
+        // packed pairs: the Wendland kernel (the Sinc kernel takes the scalar loop)
+        if (KERN == SPH_KERNEL_WENDLAND) {
         float2 px = p2(0.0f), py = p2(0.0f), pz = p2(0.0f), pu = p2(0.0f);
 #pragma unroll
         for (int hh = 0; hh < 2; hh++) {
@@ -482,7 +611,8 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         by = py.x + py.y;
         bz = pz.x + pz.y;
         bu = pu.x + pu.y;
-#else
+        } else
+#endif
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             if (base + (uint32_t)u >= len) break;
@@ -497,13 +627,12 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
                 rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
             else
                 rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-            const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K);
+            const PairTerms t = momentum_pair<KERN>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
             bx += t.ax;
             by += t.ay;
             bz += t.az;
             bu += t.du;
         }
-#endif
         kahan_add(A.sx, A.cx, bx);
         kahan_add(A.sy, A.cy, by);
         kahan_add(A.sz, A.cz, bz);
@@ -523,7 +652,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
             rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
         else
             rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-        const PairTerms t = momentum_pair(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K);
+        const PairTerms t = momentum_pair<KERN>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
         kahan_add(A.sx, A.cx, t.ax);
         kahan_add(A.sy, A.cy, t.ay);
         kahan_add(A.sz, A.cz, t.az);
@@ -535,9 +664,10 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
 #ifndef SPH_MOM_MINB
 #define SPH_MOM_MINB 2                  // resident 256-thread CTAs per SM the registers are sized for
 #endif
-template <int TPP>
+template <int TPP, int KERN>
 __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a)
 {
+    const float gscale = (float)KernF<KERN>::grad_scale(a.kb, a.kernel_n);
     __shared__ float4 tab[kStencilCells];
     fill_stencil_table(tab);
     if (*a.status & kStBad) return;
@@ -561,16 +691,16 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
         const uint32_t ci = a.cellxyz[i];
         MomAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (P->zmode)
-            momentum_row<TPP, 1>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
+            momentum_row<TPP, 1, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
         else
-            momentum_row<TPP, 0>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
+            momentum_row<TPP, 0, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
         group_kahan_reduce<TPP>(A.sx, A.cx, G.gmask);
         group_kahan_reduce<TPP>(A.sy, A.cy, G.gmask);
         group_kahan_reduce<TPP>(A.sz, A.cz, G.gmask);
         group_kahan_reduce<TPP>(A.su, A.cu, G.gmask);
         if (G.gl == 0) {
-            const float4 r = make_float4(k80Sigma * (A.sx - A.cx), k80Sigma * (A.sy - A.cy), k80Sigma * (A.sz - A.cz),
-                                         k80Sigma * (A.su - A.cu));
+            const float4 r = make_float4(gscale * (A.sx - A.cx), gscale * (A.sy - A.cy), gscale * (A.sz - A.cz),
+                                         gscale * (A.su - A.cu));
             a.r.acc[i] = r;
             if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(r.z) || !isfinite(r.w))
                 atomicOr(a.status, kStNonFinite);
@@ -581,13 +711,14 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
 // ---------------------------------------------------------------------------
 // A7, FP64
 // ---------------------------------------------------------------------------
-template <int TPP>
+template <int TPP, int KERN>
 __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
 {
     if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
-    const double S80 = 80.0 * kSigmaW;
+    const int kn = a.kernel_n;
+    const double S80 = KernF<KERN>::grad_scale(a.kb, kn);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
         const PatchDev* P = a.pd + a.patch_of[i];
         const double lz = P->lz, hl = 0.5 * P->lz;
@@ -608,9 +739,7 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
             const double r2 = dx * dx + dy * dy + dz * dz;
             const double r = sqrt(r2);
             const double wj = 0.5 * a.f.invh[j];
-            const double qi = fmax(1.0 - r * wi, 0.0);
-            const double qj = fmax(1.0 - r * wj, 0.0);
-            const double F = wi5 * qi * qi * qi + wj * wj * wj * wj * wj * qj * qj * qj;
+            const double F = KernF<KERN>::grad(r, wi, wi5, kn) + KernF<KERN>::grad(r, wj, wj * wj * wj * wj * wj, kn);
             const double vx = vxi - a.f.vhx[j], vy = vyi - a.f.vhy[j], vz = vzi - a.f.vhz[j];
             const double vdot = vx * dx + vy * dy + vz * dz;
             double pi_ = 0.0;
@@ -642,14 +771,20 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
     }
 }
 
-#define SPH_DISPATCH_TPP(KERNEL, tpp, blocks, L, a)                                   \
-    switch (tpp) {                                                                    \
-    case 1: KERNEL<1><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
-    case 2: KERNEL<2><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
-    case 4: KERNEL<4><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
-    case 16: KERNEL<16><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
-    case 32: KERNEL<32><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
-    default: KERNEL<8><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;         \
+#define SPH_DISPATCH_TPP(KERNEL, KERN, tpp, blocks, L, a)                                   \
+    switch (tpp) {                                                                          \
+    case 1: KERNEL<1, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 2: KERNEL<2, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 4: KERNEL<4, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 16: KERNEL<16, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
+    case 32: KERNEL<32, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
+    default: KERNEL<8, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;         \
+    }
+#define SPH_DISPATCH(KERNEL, tpp, blocks, L, a)                                             \
+    if ((a).kernel == SPH_KERNEL_SINC) {                                                    \
+        SPH_DISPATCH_TPP(KERNEL, SPH_KERNEL_SINC, tpp, blocks, L, a);                       \
+    } else {                                                                                \
+        SPH_DISPATCH_TPP(KERNEL, SPH_KERNEL_WENDLAND, tpp, blocks, L, a);                   \
     }
 
 static int64_t pair_blocks(const Launch& L, int64_t n, int tpp)
@@ -666,9 +801,9 @@ int launch_density(const Launch& L, const PairArgs& a, int tpp, int mixed)
     if (a.n <= 0) return 0;
     const int64_t blocks = pair_blocks(L, a.n, tpp);
     if (mixed) {
-        SPH_DISPATCH_TPP(k_density_mixed, tpp, blocks, L, a);
+        SPH_DISPATCH(k_density_mixed, tpp, blocks, L, a);
     } else {
-        SPH_DISPATCH_TPP(k_density_fp64, tpp, blocks, L, a);
+        SPH_DISPATCH(k_density_fp64, tpp, blocks, L, a);
     }
     return 1;
 }
@@ -678,9 +813,9 @@ int launch_momentum(const Launch& L, const PairArgs& a, int tpp, int mixed)
     if (a.n <= 0) return 0;
     const int64_t blocks = pair_blocks(L, a.n, tpp);
     if (mixed) {
-        SPH_DISPATCH_TPP(k_momentum_mixed, tpp, blocks, L, a);
+        SPH_DISPATCH(k_momentum_mixed, tpp, blocks, L, a);
     } else {
-        SPH_DISPATCH_TPP(k_momentum_fp64, tpp, blocks, L, a);
+        SPH_DISPATCH(k_momentum_fp64, tpp, blocks, L, a);
     }
     return 1;
 }

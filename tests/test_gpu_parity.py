@@ -198,6 +198,36 @@ def test_step_density_matches(B, orc, case, report):
         assert v < 1e-5, (k, v)
 
 
+@pytest.mark.parametrize("case", ["patch20", "cloud_av", "irregular", "htail_near"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_sinc_kernel_pair_sums(B, orc, case, precision, tol, report):
+    """The Sinc kernel of Sec. 3 (n = 6) in the density and momentum sums."""
+    f = FORCE_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    g = _gpu_forces(B, f, precision, lz=lz, kernel="sinc", kernel_n=6)
+    with orc.kernel("sinc", 6):
+        o = _oracle_forces(orc, f, lz)
+    _check_forces(g, o, tol, report, "sinc/%s/%s" % (precision, case))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+def test_sinc_kernel_ten_steps(B, orc, precision, tol, report):
+    f = inputs.square_patch(20)
+    sim = B.SPH(len(f["x"]), precision=precision, kernel="sinc", kernel_n=6)
+    sim.set_particles(f)
+    ref = orc.Sim(f, kernel="sinc", kernel_n=6)
+    hist = []
+    for step in range(10):
+        dt = sim.step(1)
+        ref.step(1)
+        assert abs(dt - ref.dt) <= tol * ref.dt, (step, dt, ref.dt)
+        g = {k: sim.field(k) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "nown", "rho",
+                                       "ax", "ay", "az")}
+        hist.append(_compare_state(g, ref, tol, "sinc step %d" % step))
+    report["sinc_steps10/%s" % precision] = hist
+    sim.close()
+
+
 def _compare_state(g, o, tol, what):
     errs = {k: normwise(g[k], o[k]) for k in ("x", "y", "u", "h", "rho")}
     errs["v"] = normwise_vec([g["vx"], g["vy"], g["vz"]], [o["vx"], o["vy"], o["vz"]])
