@@ -36,6 +36,10 @@ SM_MAX_MHZ = 2070.0
 # design notes)
 FLOPS_PER_PAIR_MOMENTUM = 70
 FLOPS_PER_PAIR_DENSITY = 28
+# the Sinc kernel (n = 6) in k_momentum_mixed: the Wendland count with its
+# gradient shape (12) replaced by two sides of x = pi r w, S = sin x / x,
+# S^5, g(x) and w^5 S^5 g (15 each) plus w_j^5 (3) and their sum (1)
+FLOPS_PER_PAIR_MOMENTUM_SINC = 92
 # FP64 operations per pair of k_momentum_fp64 (mul/add each 1, sqrt and
 # divisions not counted): 47 on every pair plus 17 for the viscosity of
 # approaching pairs, taken on half of them
@@ -209,6 +213,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--kernel", default="wendland", choices=["wendland", "sinc"],
+                    help="SPH kernel of Sec. 3 (Sinc with n = 6)")
     ap.add_argument("--cell-factor", type=float, default=0.0,
                     help="fixed cell factor (implies --no-autotune); 0 = tuned")
     ap.add_argument("--tpp", type=int, default=0,
@@ -239,7 +245,7 @@ def main():
     dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
 
     def make(precision, graph=False):
-        kw = {}
+        kw = {"kernel": args.kernel, "kernel_n": 6}
         if args.cell_factor:
             kw["cell_factor"] = args.cell_factor
         if args.tpp:
@@ -333,14 +339,15 @@ def main():
             "share_of_step": prof["nb"][0] / ms_total}
     # the pair sums: FP32 pipe (mixed) against the derived FP32 peak
     mom_ms = prof["momentum"][0] / max(args.steps, 1)
-    mom_tf = FLOPS_PER_PAIR_MOMENTUM * pairs_per_step / (mom_ms / 1e3) / 1e12
+    flops_pair = FLOPS_PER_PAIR_MOMENTUM_SINC if args.kernel == "sinc" else FLOPS_PER_PAIR_MOMENTUM
+    mom_tf = flops_pair * pairs_per_step / (mom_ms / 1e3) / 1e12
     roof_mom = {"bound": "alu", "kernel": "k_momentum_mixed" if args.precision == "mixed" else "k_momentum_fp64",
                 "achieved": mom_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak,
                 "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step) if MOMENTUM_DRAM_BYTES_PER_ENTRY else None,
                 "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
                                % (SMS, FP32_LANES_PER_SM, sm_max),
                 "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf / fma_peak,
-                "flops_per_pair": FLOPS_PER_PAIR_MOMENTUM, "ms_per_launch": mom_ms,
+                "flops_per_pair": flops_pair, "ms_per_launch": mom_ms,
                 "share_of_step": prof["momentum"][0] / ms_total}
     if clk.get("sm_mhz"):
         roof_mom["frac_at_sampled_clock"] = mom_tf / (fp32_peak * clk["sm_mhz"] / sm_max)
@@ -352,7 +359,7 @@ def main():
         "dtype": "f32-mixed (f32 pair sums + Kahan, f64 positions/integration/reductions)"
         if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": wl, "particles": n, "precision": args.precision,
+        "config": {"workload": wl, "particles": n, "precision": args.precision, "kernel": args.kernel,
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
