@@ -29,7 +29,7 @@ class OrcParams(ctypes.Structure):
                 ("av_alpha", ctypes.c_double), ("av_beta", ctypes.c_double),
                 ("av_eps", ctypes.c_double), ("lz", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("adapt_h", ctypes.c_int32),
-                ("use_grid", ctypes.c_int32)]
+                ("use_grid", ctypes.c_int32), ("grad_h", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class OrcState(ctypes.Structure):
@@ -64,8 +64,12 @@ def lib():
         L.orc_eos.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D]
         L.orc_momentum_energy.restype = None
         L.orc_momentum_energy.argtypes = ([ctypes.c_int64] + [_D] * 11 +
-                                          [ctypes.c_double] * 4 + [_I64, _I32] + [_D] * 6 +
+                                          [ctypes.c_double] * 4 + [_I64, _I32] + [_D] * 7 +
                                           [ctypes.c_int])
+        L.orc_omega.restype = None
+        L.orc_omega.argtypes = [ctypes.c_int64] + [_D] * 6 + [ctypes.c_double, _I64, _I32, _D, ctypes.c_int]
+        L.orc_dwdh.restype = ctypes.c_double
+        L.orc_dwdh.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_courant.restype = ctypes.c_double
         L.orc_courant.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double]
         L.orc_conserved.restype = None
@@ -187,15 +191,33 @@ def eos(rho, u, gamma=5.0 / 3.0):
 
 
 def momentum_energy(x, y, z, vx, vy, vz, m, h, rho, P, c, nb, lz=1.0, alpha=1.0, beta=2.0,
-                    eps=0.01, nthreads=1):
-    """Returns (ax, ay, az, du, sa, sdu); sa/sdu are the term-magnitude sums."""
+                    eps=0.01, nthreads=1, omega=None):
+    """Returns (ax, ay, az, du, sa, sdu); sa/sdu are the term-magnitude sums.
+    With omega (from omega()), the grad-h form (R20)."""
     arrs = list(map(_f64, (x, y, z, vx, vy, vz, m, h, rho, P, c)))
     n = len(arrs[0])
     outs = [np.zeros(n) for _ in range(6)]
+    om = _f64(omega) if omega is not None else None
     lib().orc_momentum_energy(n, *[_d(a) for a in arrs], lz, alpha, beta, eps,
                               nb.off.ctypes.data_as(_I64), nb.col.ctypes.data_as(_I32),
+                              _d(om) if om is not None else None,
                               *[_d(o) for o in outs], nthreads)
     return tuple(outs)
+
+
+def omega(x, y, z, m, h, rho, nb, lz=1.0, nthreads=1):
+    """Grad-h factor Omega_i = 1 + h_i/(3 rho_i) sum_j m_j dW_ij(h_i)/dh_i (R20)."""
+    arrs = list(map(_f64, (x, y, z, m, h, rho)))
+    n = len(arrs[0])
+    out = np.zeros(n)
+    lib().orc_omega(n, *[_d(a) for a in arrs], lz, nb.off.ctypes.data_as(_I64),
+                    nb.col.ctypes.data_as(_I32), _d(out), nthreads)
+    return out
+
+
+def dwdh(r, h):
+    """dW/dh at fixed r for the current kernel."""
+    return lib().orc_dwdh(float(r), float(h))
 
 
 def courant(h, c, C=0.2):
@@ -220,7 +242,7 @@ class Sim:
 
     def __init__(self, fields, gamma=5.0 / 3.0, n_target=100.0, courant=0.2, dt_growth=1.1,
                  av_alpha=1.0, av_beta=2.0, av_eps=0.01, lz=1.0, adapt_h=True, dt_fixed=0.0,
-                 use_grid=-1, nthreads=1, kernel="wendland", kernel_n=6):
+                 use_grid=-1, nthreads=1, kernel="wendland", kernel_n=6, grad_h=False):
         n = len(fields["x"])
         self.n = n
         self.arr = {}
@@ -233,7 +255,7 @@ class Sim:
             self.arr[k] = np.zeros(n)
         self.arr["nown"] = np.zeros(max(n, 1), dtype=np.int32)
         self.params = OrcParams(gamma, n_target, courant, dt_growth, av_alpha, av_beta, av_eps,
-                                lz, dt_fixed, int(bool(adapt_h)), int(use_grid))
+                                lz, dt_fixed, int(bool(adapt_h)), int(use_grid), int(bool(grad_h)), 0)
         self.st = OrcState()
         self.st.n = n
         for k in STATE_FIELDS + OUT_FIELDS:

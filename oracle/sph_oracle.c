@@ -25,7 +25,10 @@
  *                               SPH", Table 1 "Standard" volume elements; R1)
  *   orc_eos ................... ideal gas (R9)
  *   orc_momentum_energy ....... momentum eq. [rosswog2009] + artificial
- *                               viscosity [monaghan1983], Sec. 3 (R4-R6)
+ *                               viscosity [monaghan1983], Sec. 3 (R4-R6); with
+ *                               an Omega array, the grad-h form of the same
+ *                               reference (R20)
+ *   orc_dwdh, orc_omega ....... dW/dh and the grad-h factor Omega (R20)
  *   orc_courant ............... Courant condition, global time-step (Sec. 3,
  *                               Table 1 "Global"; R7)
  *   orc_step .................. Press (leapfrog) positions, Adams-Bashforth
@@ -169,6 +172,28 @@ double orc_gradw_fac(double r, double h)
     double q = 1.0 - 0.5 * v;
     double h2 = h * h;
     return 5.0 * orc_sigma_w() / (h2 * h2 * h) * (q * q * q);
+}
+
+/* dW/dh at fixed r.  W = K/h^3 F(v), v = r/h:  dW/dh = -K/h^4 (3 F + v F'(v)).
+ * Wendland: F = (1 - v/2)^4 (2v + 1), F' = -5 v (1 - v/2)^3.
+ * Sinc: F = S^n(x), x = pi v/2, v F' = n S^(n-1) x S'(x) = -n S^(n-1) x^2 g(x),
+ * g = (sin x - x cos x)/x^3.                                                 */
+double orc_dwdh(double r, double h)
+{
+    double v = r / h;
+    if (v >= 2.0) return 0.0;
+    double h4 = h * h * h * h;
+    if (g_kernel == ORC_SINC) {
+        double x = 0.5 * M_PI * v;
+        double S = sinc_of(x);
+        double F = ipow(S, g_sinc_n);
+        double vF = -g_sinc_n * ipow(S, g_sinc_n - 1) * x * x * sinc_slope(x);
+        return -g_sinc_bn / h4 * (3.0 * F + vF);
+    }
+    double q = 1.0 - 0.5 * v;
+    double F = q * q * q * q * (2.0 * v + 1.0);
+    double vF = -5.0 * v * v * q * q * q;
+    return -orc_sigma_w() / h4 * (3.0 * F + vF);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -425,6 +450,43 @@ void orc_density(int64_t n, const double* x, const double* y, const double* z, c
     free(acc);
 }
 
+/* R20 (grad-h, [rosswog2009]):
+ *   Omega_i = 1 - (dh_i/drho_i) sum_j m_j dW_ij(h_i)/dh_i,  dh/drho = -h/(3 rho)
+ * (h proportional to rho^(-1/3), the relation behind the neighbour-number
+ * rule R10); the sum runs over j in N(i) and j = i (the self term
+ * dW(0, h)/dh = -3 W(0, h)/h).  rho from orc_density.                       */
+void orc_omega(int64_t n, const double* x, const double* y, const double* z, const double* m,
+               const double* h, const double* rho, double lz, const int64_t* off, const int32_t* col,
+               double* omega, int nthreads)
+{
+    int T = nthreads_eff(nthreads);
+    double* acc = (double*)calloc((size_t)T * (size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel num_threads(T)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double* a = acc + (size_t)t * (size_t)n;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t k = off[i]; k < off[i + 1]; k++) {
+                int64_t j = col[k];
+                if (j <= i) continue;
+                double r = sqrt(pair_r2(x[i], y[i], z[i], x[j], y[j], z[j], lz));
+                a[i] += m[j] * orc_dwdh(r, h[i]);
+                a[j] += m[i] * orc_dwdh(r, h[j]);
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; i++) {
+        double s = m[i] * orc_dwdh(0.0, h[i]);
+        for (int t = 0; t < T; t++) s += acc[(size_t)t * (size_t)n + (size_t)i];
+        omega[i] = 1.0 + h[i] / (3.0 * rho[i]) * s;
+    }
+    free(acc);
+}
+
 /* R9: ideal gas, P = (gamma - 1) rho u, c = sqrt(gamma P / rho) */
 void orc_eos(int64_t n, const double* rho, const double* u, double gamma, double* P, double* c)
 {
@@ -450,6 +512,10 @@ static double av_pi(double vdotr, double r2, double hi, double hj, double ci, do
 /* R4-R6.  With Wbar_ij = (W(r,h_i) + W(r,h_j))/2 and A = P/rho^2:
  *   a_i  = - sum_j m_j (A_i + A_j + Pi_ij) grad_i Wbar_ij
  *   du_i =   sum_j m_j (A_i + Pi_ij/2) v_ij . grad_i Wbar_ij
+ * R20, when omega != NULL (grad-h form, each side's pressure term with its
+ * own kernel, W_i = W(r, h_i), W_j = W(r, h_j)):
+ *   a_i  = - sum_j m_j (A_i/Omega_i grad_i W_i + A_j/Omega_j grad_i W_j + Pi_ij grad_i Wbar_ij)
+ *   du_i =   sum_j m_j (A_i/Omega_i v_ij . grad_i W_i + Pi_ij/2 v_ij . grad_i Wbar_ij)
  * Optional outputs sa, sdu (may be NULL) are per-particle condition scales:
  *   sa_i  = sum_j m_j |A_i + A_j + Pi_ij| |grad_i Wbar_ij|
  *   sdu_i = sum_j m_j |A_i + Pi_ij/2| |v_ij| |grad_i Wbar_ij|
@@ -459,8 +525,8 @@ void orc_momentum_energy(int64_t n, const double* x, const double* y, const doub
                          const double* vx, const double* vy, const double* vz, const double* m,
                          const double* h, const double* rho, const double* P, const double* c,
                          double lz, double alpha, double beta, double eps, const int64_t* off,
-                         const int32_t* col, double* ax, double* ay, double* az, double* du,
-                         double* sa, double* sdu, int nthreads)
+                         const int32_t* col, const double* omega, double* ax, double* ay, double* az,
+                         double* du, double* sa, double* sdu, int nthreads)
 {
     int T = nthreads_eff(nthreads);
     const int NF = 6;
@@ -491,29 +557,55 @@ void orc_momentum_energy(int64_t n, const double* x, const double* y, const doub
                 else if (dz < -0.5 * lz) dz += lz;
                 double r2 = (dx * dx + dy * dy) + dz * dz;
                 double r = sqrt(r2);
-                /* grad_i Wbar_ij = -(f(h_i) + f(h_j))/2 * x_ij ; grad_j Wbar_ji = -grad_i Wbar_ij */
-                double f = 0.5 * (orc_gradw_fac(r, h[i]) + orc_gradw_fac(r, h[j]));
-                double gx = -f * dx, gy = -f * dy, gz = -f * dz;
                 double vxij = vx[i] - vx[j], vyij = vy[i] - vy[j], vzij = vz[i] - vz[j];
                 double vdotr = vxij * dx + vyij * dy + vzij * dz;
-                double Pi = av_pi(vdotr, r2, h[i], h[j], c[i], c[j], rho[i], rho[j], alpha, beta, eps);
-                double s = Ai + Aj + Pi;
-                /* particle i */
-                bx[i] -= m[j] * s * gx;
-                by[i] -= m[j] * s * gy;
-                bz[i] -= m[j] * s * gz;
-                bu[i] += m[j] * (Ai + 0.5 * Pi) * (vxij * gx + vyij * gy + vzij * gz);
-                /* particle j: grad_j Wbar_ji = -g, v_ji = -v_ij */
-                bx[j] -= m[i] * s * (-gx);
-                by[j] -= m[i] * s * (-gy);
-                bz[j] -= m[i] * s * (-gz);
-                bu[j] += m[i] * (Aj + 0.5 * Pi) * ((-vxij) * (-gx) + (-vyij) * (-gy) + (-vzij) * (-gz));
-                double gn = f * r;
                 double vn = sqrt(vxij * vxij + vyij * vyij + vzij * vzij);
-                ba[i] += m[j] * fabs(s) * gn;
-                ba[j] += m[i] * fabs(s) * gn;
-                bd[i] += m[j] * fabs(Ai + 0.5 * Pi) * vn * gn;
-                bd[j] += m[i] * fabs(Aj + 0.5 * Pi) * vn * gn;
+                if (!omega) {
+                    /* grad_i Wbar_ij = -(f(h_i) + f(h_j))/2 * x_ij ; grad_j Wbar_ji = -grad_i Wbar_ij */
+                    double f = 0.5 * (orc_gradw_fac(r, h[i]) + orc_gradw_fac(r, h[j]));
+                    double gx = -f * dx, gy = -f * dy, gz = -f * dz;
+                    double Pi = av_pi(vdotr, r2, h[i], h[j], c[i], c[j], rho[i], rho[j], alpha, beta, eps);
+                    double s = Ai + Aj + Pi;
+                    /* particle i */
+                    bx[i] -= m[j] * s * gx;
+                    by[i] -= m[j] * s * gy;
+                    bz[i] -= m[j] * s * gz;
+                    bu[i] += m[j] * (Ai + 0.5 * Pi) * (vxij * gx + vyij * gy + vzij * gz);
+                    /* particle j: grad_j Wbar_ji = -g, v_ji = -v_ij */
+                    bx[j] -= m[i] * s * (-gx);
+                    by[j] -= m[i] * s * (-gy);
+                    bz[j] -= m[i] * s * (-gz);
+                    bu[j] += m[i] * (Aj + 0.5 * Pi) * ((-vxij) * (-gx) + (-vyij) * (-gy) + (-vzij) * (-gz));
+                    double gn = f * r;
+                    ba[i] += m[j] * fabs(s) * gn;
+                    ba[j] += m[i] * fabs(s) * gn;
+                    bd[i] += m[j] * fabs(Ai + 0.5 * Pi) * vn * gn;
+                    bd[j] += m[i] * fabs(Aj + 0.5 * Pi) * vn * gn;
+                } else {
+                    /* R20: grad_i W(r, h) = -f(h) x_ij for each side's own kernel,
+                     * grad_i Wbar_ij = -(f_i + f_j)/2 x_ij; the pair force is a
+                     * multiple k of x_ij: a_i -= m_j k x_ij, a_j += m_i k x_ij   */
+                    double fi = orc_gradw_fac(r, h[i]), fj = orc_gradw_fac(r, h[j]);
+                    double f = 0.5 * (fi + fj);
+                    double Pi = av_pi(vdotr, r2, h[i], h[j], c[i], c[j], rho[i], rho[j], alpha, beta, eps);
+                    double Bi = Ai / omega[i], Bj = Aj / omega[j];
+                    double kf = -(Bi * fi + Bj * fj + Pi * f);
+                    double ei = -(Bi * fi + 0.5 * Pi * f);
+                    double ej = -(Bj * fj + 0.5 * Pi * f);
+                    bx[i] -= m[j] * kf * dx;
+                    by[i] -= m[j] * kf * dy;
+                    bz[i] -= m[j] * kf * dz;
+                    bu[i] += m[j] * ei * vdotr;
+                    bx[j] += m[i] * kf * dx;
+                    by[j] += m[i] * kf * dy;
+                    bz[j] += m[i] * kf * dz;
+                    bu[j] += m[i] * ej * vdotr;
+                    double sk = (fabs(Bi * fi) + fabs(Bj * fj) + fabs(Pi * f)) * r;
+                    ba[i] += m[j] * sk;
+                    ba[j] += m[i] * sk;
+                    bd[i] += m[j] * (fabs(Bi * fi) + fabs(0.5 * Pi * f)) * r * vn;
+                    bd[j] += m[i] * (fabs(Bj * fj) + fabs(0.5 * Pi * f)) * r * vn;
+                }
             }
         }
     }
@@ -584,6 +676,8 @@ typedef struct {
     double dt_fixed; /* > 0: use this dt instead of the Courant condition */
     int32_t adapt_h;
     int32_t use_grid; /* 0 brute force, 1 grid, -1 grid when n > 5000 */
+    int32_t grad_h;   /* 1: the grad-h momentum and energy form (R20) */
+    int32_t pad;
 } orc_params;
 
 typedef struct {
@@ -635,9 +729,16 @@ int orc_step(const orc_params* prm, orc_state* s, int nthreads)
         vh[n + i] = s->vy[i] + s->ayp[i] * half;
         vh[2 * n + i] = s->vz[i] + s->azp[i] * half;
     }
+    double* om = NULL;
+    if (prm->grad_h) {
+        om = (double*)malloc((size_t)n * sizeof(double));
+        if (!om) { free(vh); free(col); free(off); return -1; }
+        orc_omega(n, s->x, s->y, s->z, s->m, s->h, s->rho, prm->lz, off, col, om, nthreads);
+    }
     orc_momentum_energy(n, s->x, s->y, s->z, vh, vh + n, vh + 2 * n, s->m, s->h, s->rho, s->P,
-                        s->c, prm->lz, prm->av_alpha, prm->av_beta, prm->av_eps, off, col, s->ax,
+                        s->c, prm->lz, prm->av_alpha, prm->av_beta, prm->av_eps, off, col, om, s->ax,
                         s->ay, s->az, s->du, NULL, NULL, nthreads);
+    free(om);
     free(vh);
     free(col);
     free(off);

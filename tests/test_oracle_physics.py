@@ -144,3 +144,79 @@ def test_courant(orc):
     h = np.array([0.1, 0.2, 0.05])
     c = np.array([1.0, 1.0, 2.0])
     assert orc.courant(h, c, 0.2) == pytest.approx(0.2 * 0.025, rel=1e-15)
+
+
+# ---- the grad-h form (reading R20): Omega and the per-side pressure terms ----
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+def test_dwdh_is_derivative(orc, kernel):
+    with orc.kernel(kernel, 6):
+        for h in (1.0, 0.07):
+            for v in np.linspace(0.0, 1.95, 21):
+                r = v * h
+                d = 1e-6 * h
+                fd = (orc.w(r, h + d) - orc.w(r, h - d)) / (2 * d)
+                assert orc.dwdh(r, h) == pytest.approx(fd, rel=1e-6, abs=1e-8 / h ** 4)
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+def test_omega_is_the_density_derivative(orc, kernel):
+    # Omega_i = 1 + h_i/(3 rho_i) d rho_i / d h_i: a central difference of the
+    # density itself (lists of the larger h, a superset) must agree
+    f = inputs.random_cloud(800, seed=7, h_lo=0.08, h_hi=0.12)
+    with orc.kernel(kernel, 6):
+        d = 1e-5
+        big = orc.neighbors(f["x"], f["y"], f["z"], f["h"] * (1 + 2 * d))
+        rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], big)
+        rp = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"] * (1 + d), big)
+        rm = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"] * (1 - d), big)
+        om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, big)
+    # rho_i depends on h_i only (W(r, h_i)): d rho / d h_i by the scaled-h difference
+    fd = 1.0 + f["h"] / (3 * rho) * (rp - rm) / (2 * d * f["h"])
+    assert np.allclose(om, fd, rtol=0, atol=1e-6)
+    assert np.all(np.abs(om - 1.0) > 1e-3)     # not trivially one in a random cloud
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+def test_omega_near_one_on_a_lattice(orc, kernel):
+    n = 16
+    f = inputs.square_patch(n)
+    with orc.kernel(kernel, 6):
+        nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+        rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+        om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, nb)
+    interior = (np.abs(f["x"]) < 0.5 - 3.5 / n) & (np.abs(f["y"]) < 0.5 - 3.5 / n)
+    assert np.all(np.abs(om[interior] - 1.0) < 0.05)
+
+
+def test_gradh_with_unit_omega_and_equal_h_is_the_standard_form(orc):
+    # with Omega = 1 and one h for all, A_i grad W_i + A_j grad W_j = (A_i + A_j) grad Wbar
+    f = inputs.random_cloud(600, seed=9, h_lo=0.1, h_hi=0.1, vscale=2.0)
+    std = _all(orc, f)
+    gh = orc.momentum_energy(f["x"], f["y"], f["z"], f["vx"], f["vy"], f["vz"], f["m"], f["h"],
+                             std["rho"], std["P"], std["c"], std["nb"], omega=np.ones(len(f["x"])))
+    scale = np.maximum(std["sa"], 1e-300)
+    for k, comp in enumerate(("ax", "ay", "az")):
+        assert np.max(np.abs(gh[k] - std[comp]) / scale) < 1e-13
+    assert np.max(np.abs(gh[3] - std["du"]) / np.maximum(std["sdu"], 1e-300)) < 1e-13
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+def test_gradh_conserves_momentum_and_energy(orc, kernel):
+    f = inputs.random_cloud(1000, seed=11, vscale=3.0, h_lo=0.06, h_hi=0.12)
+    with orc.kernel(kernel, 6):
+        nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+        rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+        P, c = orc.eos(rho, f["u"])
+        om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, nb)
+        ax, ay, az, du, sa, sdu = orc.momentum_energy(f["x"], f["y"], f["z"], f["vx"], f["vy"], f["vz"],
+                                                      f["m"], f["h"], rho, P, c, nb, omega=om)
+    m = f["m"]
+    scale = np.sum(m * sa)
+    for a in (ax, ay, az):
+        assert abs(np.sum(m * a)) < 1e-13 * scale
+    assert abs(np.sum(m * (f["x"] * ay - f["y"] * ax))) < 1e-13 * scale
+    vdota = f["vx"] * ax + f["vy"] * ay + f["vz"] * az
+    vmag = np.sqrt(f["vx"] ** 2 + f["vy"] ** 2 + f["vz"] ** 2)
+    total = np.sum(m * (vdota + du))
+    assert abs(total) < 1e-13 * np.sum(m * (vmag * sa + sdu))
