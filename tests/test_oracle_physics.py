@@ -220,3 +220,49 @@ def test_gradh_conserves_momentum_and_energy(orc, kernel):
     vmag = np.sqrt(f["vx"] ** 2 + f["vy"] ** 2 + f["vz"] ** 2)
     total = np.sum(m * (vdota + du))
     assert abs(total) < 1e-13 * np.sum(m * (vmag * sa + sdu))
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+def test_omega_of_an_isolated_particle_is_zero(orc, kernel):
+    # the self term alone: rho = m W(0, h), dW(0, h)/dh = -3 W(0, h)/h, so
+    # Omega = 1 + h/(3 m W(0)) m (-3 W(0)/h) = 0
+    f = {k: np.zeros(2) for k in ("x", "y", "z", "vx", "vy", "vz")}
+    f.update(x=np.array([0.1, 0.7]), m=np.array([0.5, 0.25]), h=np.array([0.1, 0.05]), u=np.ones(2))
+    with orc.kernel(kernel, 6):
+        nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+        assert nb.off[-1] == 0
+        rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+        om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, nb)
+    assert np.all(np.abs(om) < 4e-16)
+
+
+@pytest.mark.parametrize("v", [0.3, 0.9, 1.4, 1.9])
+def test_omega_of_a_wendland_pair(orc, v):
+    # two equal particles at r = v h: with S(v) = q^4 (5 - 4q), q = 1 - v/2,
+    # d(h^-3 S(r/h))/dh = -h^-4 (3 S + v S'(v)) and v S'(v) = -20 (1-q)^2 q^3:
+    #   Omega = 1 - (3 + 3 S - 20 (1-q)^2 q^3) / (3 (1 + S)) = 20 (1-q)^2 q^3 / (3 (1 + S))
+    h = 0.1
+    f = {k: np.zeros(2) for k in ("x", "y", "z", "vx", "vy", "vz")}
+    f.update(x=np.array([0.2, 0.2 + v * h]), m=np.full(2, 0.3), h=np.full(2, h), u=np.ones(2))
+    nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+    rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+    om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, nb)
+    q = 1.0 - v / 2.0
+    S = q ** 4 * (5.0 - 4.0 * q)
+    want = 20.0 * (1.0 - q) ** 2 * q ** 3 / (3.0 * (1.0 + S))
+    assert om == pytest.approx([want, want], rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_omega_never_negative(orc, kernel, seed):
+    # both kernel shapes decrease on their support, so each neighbour adds a
+    # non-negative -v S'(v) to Omega and the self term adds nothing: Omega >= 0
+    # up to the rounding of 1 + (a sum near -1)
+    f = inputs.random_cloud(1500, seed=seed, h_lo=0.03, h_hi=0.2)
+    with orc.kernel(kernel, 6):
+        nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
+        rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb)
+        om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, nb)
+    assert om.min() > -1e-14
+    assert om.max() > 0.5
