@@ -40,6 +40,11 @@ FLOPS_PER_PAIR_DENSITY = 28
 # gradient shape (12) replaced by two sides of x = pi r w, S = sin x / x,
 # S^5, g(x) and w^5 S^5 g (15 each) plus w_j^5 (3) and their sum (1)
 FLOPS_PER_PAIR_MOMENTUM_SINC = 92
+# the grad-h form: each side's gradient shape on its own (+2 for the Wendland
+# kernel: w_j^5 and the sum; the Sinc count already has both) and the
+# pressure terms 2 A_i f_i + 2 A_j f_j + Pi F and 2 A_i f_i + Pi F / 2 (+4)
+FLOPS_PER_PAIR_MOMENTUM_GRADH = 76
+FLOPS_PER_PAIR_MOMENTUM_SINC_GRADH = 96
 # FP64 operations per pair of k_momentum_fp64 (mul/add each 1, sqrt and
 # divisions not counted): 47 on every pair plus 17 for the viscosity of
 # approaching pairs, taken on half of them
@@ -127,12 +132,17 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline_1thread(sample_n=40, nsteps=1):
+def oracle_kw(args):
+    """The oracle's kernel and momentum form for the bench's options."""
+    return {"kernel": args.kernel, "kernel_n": 6, "grad_h": bool(args.grad_h)}
+
+
+def cpu_baseline_1thread(args, sample_n=40, nsteps=1):
     """The same oracle step on one host core, on the 40^3 patch."""
     import oracle
     from paper_1905_03344_gb300 import inputs
     f = inputs.square_patch(sample_n)
-    sim = oracle.Sim(f, nthreads=1)
+    sim = oracle.Sim(f, nthreads=1, **oracle_kw(args))
     t0 = time.perf_counter()
     pairs = 0
     for _ in range(nsteps):
@@ -144,14 +154,14 @@ def cpu_baseline_1thread(sample_n=40, nsteps=1):
                       % (nsteps, sample_n, sample_n ** 3, dt)}
 
 
-def cpu_baseline(sample_n=100, nsteps=1):
+def cpu_baseline(args, sample_n=100, nsteps=1):
     """The FP64 oracle (as it stands) on host cores, one full step on the
     100^3 patch: the same rotating-patch workload at 1/8 of the particles."""
     import oracle
     from paper_1905_03344_gb300 import inputs
     f = inputs.square_patch(sample_n)
     threads = os.cpu_count() or 1
-    sim = oracle.Sim(f, nthreads=threads)
+    sim = oracle.Sim(f, nthreads=threads, **oracle_kw(args))
     t0 = time.perf_counter()
     pairs = 0
     for _ in range(nsteps):
@@ -173,7 +183,7 @@ def run_reference(args):
     n_edge = 100
     f = inputs.square_patch(n_edge)
     threads = os.cpu_count() or 1
-    sim = oracle.Sim(f, nthreads=threads)
+    sim = oracle.Sim(f, nthreads=threads, **oracle_kw(args))
     for _ in range(args.warmup):
         sim.step(1)
     t0 = time.perf_counter()
@@ -189,7 +199,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl, "precision": "fp64 (CPU oracle)",
+        "config": {"workload": wl, "precision": "fp64 (CPU oracle)", "kernel": args.kernel,
+                   "grad_h": bool(args.grad_h),
                    "sample": "%d^3 square patch per step" % n_edge},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "each step: one full FP64 oracle step on the %d^3 square patch "
@@ -215,6 +226,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel", default="wendland", choices=["wendland", "sinc"],
                     help="SPH kernel of Sec. 3 (Sinc with n = 6)")
+    ap.add_argument("--grad-h", action="store_true",
+                    help="the grad-h momentum and energy form (Omega factors)")
     ap.add_argument("--cell-factor", type=float, default=0.0,
                     help="fixed cell factor (implies --no-autotune); 0 = tuned")
     ap.add_argument("--tpp", type=int, default=0,
@@ -245,7 +258,7 @@ def main():
     dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
 
     def make(precision, graph=False):
-        kw = {"kernel": args.kernel, "kernel_n": 6}
+        kw = {"kernel": args.kernel, "kernel_n": 6, "grad_h": int(args.grad_h)}
         if args.cell_factor:
             kw["cell_factor"] = args.cell_factor
         if args.tpp:
@@ -339,11 +352,15 @@ def main():
             "share_of_step": prof["nb"][0] / ms_total}
     # the pair sums: FP32 pipe (mixed) against the derived FP32 peak
     mom_ms = prof["momentum"][0] / max(args.steps, 1)
-    flops_pair = FLOPS_PER_PAIR_MOMENTUM_SINC if args.kernel == "sinc" else FLOPS_PER_PAIR_MOMENTUM
+    flops_pair = {(False, False): FLOPS_PER_PAIR_MOMENTUM, (True, False): FLOPS_PER_PAIR_MOMENTUM_SINC,
+                  (False, True): FLOPS_PER_PAIR_MOMENTUM_GRADH,
+                  (True, True): FLOPS_PER_PAIR_MOMENTUM_SINC_GRADH}[(args.kernel == "sinc", args.grad_h)]
     mom_tf = flops_pair * pairs_per_step / (mom_ms / 1e3) / 1e12
     roof_mom = {"bound": "alu", "kernel": "k_momentum_mixed" if args.precision == "mixed" else "k_momentum_fp64",
                 "achieved": mom_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak,
-                "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step) if MOMENTUM_DRAM_BYTES_PER_ENTRY else None,
+                # the DRAM figure is the standard Wendland variant's
+                "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step)
+                if MOMENTUM_DRAM_BYTES_PER_ENTRY and args.kernel == "wendland" and not args.grad_h else None,
                 "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
                                % (SMS, FP32_LANES_PER_SM, sm_max),
                 "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf / fma_peak,
@@ -360,6 +377,7 @@ def main():
         if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": wl, "particles": n, "precision": args.precision, "kernel": args.kernel,
+                   "grad_h": bool(args.grad_h),
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
@@ -436,8 +454,8 @@ def main():
     sim.close()
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline()
-        line["cpu_baseline_1core"] = cpu_baseline_1thread()
+        line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_baseline_1core"] = cpu_baseline_1thread(args)
         try:
             cpu = [l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo") if l.lower().startswith(("model name", "cpu part"))]
         except OSError:

@@ -48,7 +48,9 @@ typedef enum {
     SPH_ECUDA = 3,       /* a CUDA call failed (non-sticky) */
     SPH_EOVERFLOW = 4,   /* neighbour list exceeded max_pairs; state left at the
                             start of the failing step, particles re-sorted */
-    SPH_ENONFINITE = 5,  /* NaN/Inf in density, pressure, dt or inputs */
+    SPH_ENONFINITE = 5,  /* NaN/Inf in density, pressure, dt or inputs, or
+                            (grad_h) Omega = 0: a particle with no
+                            neighbour inside its support */
     SPH_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
     SPH_ESTATE = 7       /* call out of order, or context poisoned */
 } sph_status;
@@ -84,6 +86,16 @@ typedef struct {
     double lz;              /* period along z, 1 */
     double dt_fixed;        /* > 0: fixed dt instead of the Courant condition */
     int32_t adapt_h;        /* 1: h adaptation after each step */
+    int32_t grad_h;         /* 1: the grad-h momentum and energy form of
+                               [rosswog2009]: each side's pressure term with
+                               its own kernel, divided by
+                               Omega = 1 - dh/drho sum_j m_j dW/dh (h ~ rho^-1/3),
+                               evaluated as sum_{j != i} m_j (-v S'(v)) /
+                               (3 sum_j m_j S(v)) for W = B h^-3 S(r/h), which
+                               is never negative and has no cancellation;
+                               Omega = 0 (no neighbour inside the support)
+                               fails the step with SPH_ENONFINITE;
+                               0 (default): the symmetrised-kernel form */
     int32_t threads_per_particle; /* 0 = auto; else 1, 2, 4, 8, 16 or 32 */
     double cell_factor;     /* cell edge = 2 h_s * cell_factor, in [1/3, 4]
                                (h_s: the patch's class threshold of h) */

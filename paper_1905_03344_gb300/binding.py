@@ -32,7 +32,7 @@ class SphConfig(ctypes.Structure):
                 ("courant", ctypes.c_double), ("dt_growth", ctypes.c_double),
                 ("av_alpha", ctypes.c_double), ("av_beta", ctypes.c_double),
                 ("av_eps", ctypes.c_double), ("lz", ctypes.c_double),
-                ("dt_fixed", ctypes.c_double), ("adapt_h", ctypes.c_int32),
+                ("dt_fixed", ctypes.c_double), ("adapt_h", ctypes.c_int32), ("grad_h", ctypes.c_int32),
                 ("threads_per_particle", ctypes.c_int32), ("cell_factor", ctypes.c_double),
                 ("max_particles", ctypes.c_int64), ("max_pairs", ctypes.c_int64),
                 ("max_patches", ctypes.c_int32), ("use_graph", ctypes.c_int32),

@@ -295,6 +295,7 @@ PairArgs pair_args(sph_ctx* ctx)
     a.eps = ctx->cfg.av_eps;
     a.kernel = ctx->cfg.kernel;
     a.kernel_n = ctx->cfg.kernel_n;
+    a.grad_h = ctx->cfg.grad_h;
     a.kb = ctx->kernel_b;
     a.status = ctx->status;
     return a;
@@ -599,6 +600,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         return fail(nullptr, SPH_EINVAL, "unsupported kernel");
     if (cfg.kernel == SPH_KERNEL_SINC && !(cfg.kernel_n >= 2 && cfg.kernel_n <= 16))
         return fail(nullptr, SPH_EINVAL, "kernel_n must be in [2, 16] for the Sinc kernel");
+    if (cfg.grad_h != 0 && cfg.grad_h != 1) return fail(nullptr, SPH_EINVAL, "grad_h must be 0 or 1");
     if (cfg.max_particles < 1 || cfg.max_particles > kMaxParticles)
         return fail(nullptr, SPH_EINVAL, "max_particles must be in [1, 2^25]");
     if (cfg.max_patches < 1 || cfg.max_patches > kMaxPatches)

@@ -239,6 +239,7 @@ struct PairArgs {
     Fp64 f;
     double gamma, alpha, beta, eps;
     int kernel, kernel_n;                // SPH_KERNEL_*; n of the Sinc kernel
+    int grad_h;                          // 1: grad-h form (density stores A/Omega)
     double kb;                           // sigma_W (Wendland) or B_n (Sinc)
     int* status;
 };

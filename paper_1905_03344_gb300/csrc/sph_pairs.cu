@@ -222,6 +222,20 @@ struct KernF<SPH_KERNEL_WENDLAND> {
         return w5 * q * q * q;
     }
     static __host__ __device__ double grad_scale(double kb, int) { return 80.0 * kb; }
+    // grad-h weight -v S'(v) of the shape S = q^4 (5 - 4q), q = 1 - v/2:
+    // 20 (1 - q)^2 q^3, never negative, 0 at v = 0 and v >= 2
+    static __device__ __forceinline__ float omega_w(float r, float w, int)
+    {
+        const float q = fmaxf(fmaf(-r, w, 1.0f), 0.0f);
+        const float p = 1.0f - q;
+        return 20.0f * (p * p) * (q * q * q);
+    }
+    static __device__ __forceinline__ double omega_w(double r, double w, int)
+    {
+        const double q = fmax(1.0 - r * w, 0.0);
+        const double p = 1.0 - q;
+        return 20.0 * (p * p) * (q * q * q);
+    }
 };
 
 template <>
@@ -259,6 +273,26 @@ struct KernF<SPH_KERNEL_SINC> {
         return w5 * ipowd(S, n - 1) * sinc_g(x, sn, cs);
     }
     static __host__ __device__ double grad_scale(double kb, int n) { return 4.0 * kb * n * kPi * kPi; }
+    // grad-h weight -v d(S^n)/dv = n S^(n-1) x^2 g(x) (x = pi v / 2), never
+    // negative on the support
+    static __device__ __forceinline__ float omega_w(float r, float w, int n)
+    {
+        const float x = kPif * r * w;
+        if (!(x < kPif)) return 0.0f;
+        float sn, cs;
+        __sincosf(x, &sn, &cs);
+        const float S = x > 0.0f ? __fdividef(sn, x) : 1.0f;
+        return (float)n * ipowf(S, n - 1) * (x * x) * sinc_g(x, sn, cs);
+    }
+    static __device__ __forceinline__ double omega_w(double r, double w, int n)
+    {
+        const double x = kPi * r * w;
+        if (!(x < kPi)) return 0.0;
+        double sn, cs;
+        sincos(x, &sn, &cs);
+        const double S = x > 0.0 ? sn / x : 1.0;
+        return n * ipowd(S, n - 1) * (x * x) * sinc_g(x, sn, cs);
+    }
 };
 
 // The list words stream from HBM (the pool is far larger than L2).  Each
@@ -293,13 +327,15 @@ __device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowA
 // A5 + A6, mixed precision
 // ---------------------------------------------------------------------------
 // the row of one particle: plain FP32 weights m_j W-shape(r), Kahan sum
-template <int TPP, int ZW, int KERN>
+// GH: also the sum of m_j (-v S'(v)) for the grad-h factor Omega
+template <int TPP, int ZW, int KERN, bool GH>
 __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                             int gl, float s_f, float sz_f, float lz_f, const float4& ri, float inv2h,
-                                            uint32_t ci, float& sum, float& comp)
+                                            uint32_t ci, float& sum, float& comp, float& sumd, float& compd)
 {
     const int kn = a.kernel_n;
 #if SPH_DEN_CHUNK
+    static_assert(!GH, "the chunked density loop has no grad-h sum");
     // chunks of four row words as in the momentum sum
     const uint4* row4 = reinterpret_cast<const uint4*>(row);
     const uint32_t nch = (len + 3u) >> 2;
@@ -352,12 +388,13 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
             const float r = r2 * rsqrtf(r2 + 1e-30f);
             const float m = k + (uint32_t)(u * TPP) < len ? q[u].w : 0.0f;
             kahan_fma(sum, comp, m, KernF<KERN>::dens(r, inv2h, kn));
+            if (GH) kahan_fma(sumd, compd, m, KernF<KERN>::omega_w(r, inv2h, kn));
         }
     }
 #endif
 }
 
-template <int TPP, int KERN>
+template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 {
     const float kb8 = (float)(8.0 * a.kb);
@@ -379,17 +416,30 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
         const uint32_t ci = a.cellxyz[i];
-        float sum = 0.0f, comp = 0.0f;
-        if (P->zmode) density_row<TPP, 1, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
-        else density_row<TPP, 0, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp);
+        float sum = 0.0f, comp = 0.0f, sumd = 0.0f, compd = 0.0f;
+        if (P->zmode)
+            density_row<TPP, 1, KERN, GH>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp, sumd,
+                                          compd);
+        else
+            density_row<TPP, 0, KERN, GH>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, inv2h, ci, sum, comp, sumd,
+                                          compd);
         group_kahan_reduce<TPP>(sum, comp, G.gmask);
+        if (GH) group_kahan_reduce<TPP>(sumd, compd, G.gmask);
         if (G.gl == 0) {
             const float tot = ri.w + (sum - comp);           // self term m_i W(0) ~ m_i
             const float rho = kb8 * tot * (inv2h * inv2h * inv2h);
             const float u = a.r.uf[i];                       // specific energy, staged by the gather
             const float Pr = (gam - 1.0f) * rho * u;
             const float c = sqrtf(gam * Pr / rho);
-            const float A = Pr / (rho * rho);
+            float A = Pr / (rho * rho);
+            if (GH) {
+                // R20 without cancellation: Omega = sum_j m_j (-v S'(v)) / (3 sum_j m_j S(v))
+                // (the self term adds nothing above the line); A/Omega is what the
+                // grad-h momentum sum uses
+                const float om = (sumd - compd) / (3.0f * tot);
+                A = A / om;
+                if (!(om > 0.0f)) atomicOr(a.status, kStNonFinite);
+            }
             const float hf = 0.5f / inv2h;
             a.r.rt[i] = make_float4(rho, A, c, hf);
             a.r.pf[i] = Pr;
@@ -403,7 +453,7 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 // ---------------------------------------------------------------------------
 // A5 + A6, FP64
 // ---------------------------------------------------------------------------
-template <int TPP, int KERN>
+template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
 {
     const int kn = a.kernel_n;
@@ -417,7 +467,7 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
         const double w = 0.5 * a.f.invh[i];
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
-        double sum = 0.0;
+        double sum = 0.0, sumd = 0.0;
         for (uint32_t k = G.gl; k < len; k += TPP) {
             const uint32_t j = row[k] & kColMask;
             const double dx = xi - a.s.x[j], dy = yi - a.s.y[j];
@@ -426,8 +476,10 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
             else if (dz < -hl) dz += lz;
             const double r = sqrt(dx * dx + dy * dy + dz * dz);
             sum += a.s.m[j] * KernF<KERN>::dens(r, w, kn);
+            if (GH) sumd += a.s.m[j] * KernF<KERN>::omega_w(r, w, kn);
         }
         sum = group_sum<TPP>(sum, G.gmask);
+        if (GH) sumd = group_sum<TPP>(sumd, G.gmask);
         if (G.gl == 0) {
             const double rho = a.kb * (a.s.m[i] + sum) / (hi * hi * hi);
             const double Pr = (a.gamma - 1.0) * rho * a.s.u[i];
@@ -435,7 +487,13 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
             a.f.rho[i] = rho;
             a.f.P[i] = Pr;
             a.f.c[i] = c;
-            a.f.A[i] = Pr / (rho * rho);
+            double A = Pr / (rho * rho);
+            if (GH) {
+                const double om = sumd / (3.0 * (a.s.m[i] + sum));
+                A = A / om;
+                if (!(om > 0.0)) atomicOr(a.status, kStNonFinite);
+            }
+            a.f.A[i] = A;
             a.f.hc[i] = hi / c;
             if (!(rho > 0.0) || !isfinite(rho) || !isfinite(Pr) || !isfinite(c))
                 atomicOr(a.status, kStNonFinite);
@@ -462,15 +520,22 @@ struct MomConst {
 
 // one pair of the momentum and energy sums, from x_i - x_j = (dx, dy, dz);
 // Wendland: w^5 q^3 = w^2 (w q)^3 with w q = w - r w^2
-template <int KERN>
+// GH: the grad-h form, ti.y / tj.y holding A/Omega: the pressure terms take
+// each side's own kernel gradient (2 f_i, 2 f_j in units of the symmetrised one)
+template <int KERN, bool GH>
 __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz, const float4& vi,
                                                    const float4& ti, float wi5, const float4& vj,
                                                    const float4& tj, float mj, const MomConst& K, int kn)
 {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
-    float F;
-    if (KERN == SPH_KERNEL_WENDLAND) {
+    float F, fi = 0.0f, fj = 0.0f;
+    if (GH) {
+        const float wj2 = vj.w * vj.w;
+        fi = KernF<KERN>::grad(r, vi.w, wi5, kn);
+        fj = KernF<KERN>::grad(r, vj.w, wj2 * wj2 * vj.w, kn);
+        F = fi + fj;
+    } else if (KERN == SPH_KERNEL_WENDLAND) {
         const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
         const float wj2 = vj.w * vj.w;
         const float aj = fmaxf(fmaf(-r, wj2, vj.w), 0.0f);      // w_j q_j
@@ -486,9 +551,18 @@ __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz,
     const float pi_ = vdot < 0.0f
                           ? __fdividef(m2 * fmaf(K.beta2, m2, -K.alpha2 * (ti.z + tj.z)), ti.x + tj.x)
                           : 0.0f;
+    PairTerms t;
+    if (GH) {
+        const float pi_f = pi_ * F;
+        const float fa = mj * fmaf(2.0f * ti.y, fi, fmaf(2.0f * tj.y, fj, pi_f));
+        t.ax = fa * dx;
+        t.ay = fa * dy;
+        t.az = fa * dz;
+        t.du = -mj * fmaf(2.0f * ti.y, fi, 0.5f * pi_f) * vdot;
+        return t;
+    }
     const float g = mj * F;
     const float fa = g * (ti.y + tj.y + pi_);
-    PairTerms t;
     t.ax = fa * dx;
     t.ay = fa * dy;
     t.az = fa * dz;
@@ -563,7 +637,7 @@ struct MomAcc {
 // sums the chunk's four pair terms plainly and adds that sum with Kahan
 // compensation (the plain sum of four terms errs by at most 3 eps times their
 // magnitudes, the order of one term's own rounding).
-template <int TPP, int ZW, int KERN>
+template <int TPP, int ZW, int KERN, bool GH>
 __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                              int gl, float s_f, float sz_f, float lz_f, const float4& ri,
                                              const float4& vi, const float4& ti, float wi5, const MomConst& K,
@@ -581,8 +655,9 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         const uint32_t base = ch * 4u;
         float bx = 0.0f, by = 0.0f, bz = 0.0f, bu = 0.0f;
 #if SPH_MOM_PACK
-        // packed pairs: the Wendland kernel (the Sinc kernel takes the scalar loop)
-        if (KERN == SPH_KERNEL_WENDLAND) {
+        // packed pairs: the Wendland kernel in the symmetrised form (the Sinc
+        // kernel and the grad-h form take the scalar loop)
+        if (KERN == SPH_KERNEL_WENDLAND && !GH) {
         float2 px = p2(0.0f), py = p2(0.0f), pz = p2(0.0f), pu = p2(0.0f);
 #pragma unroll
         for (int hh = 0; hh < 2; hh++) {
@@ -627,7 +702,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
                 rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
             else
                 rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-            const PairTerms t = momentum_pair<KERN>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
+            const PairTerms t = momentum_pair<KERN, GH>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
             bx += t.ax;
             by += t.ay;
             bz += t.az;
@@ -652,7 +727,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
             rel_dx<ZW>(tab[code], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
         else
             rel_dx_far(ci, a.cellxyz[j], s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-        const PairTerms t = momentum_pair<KERN>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
+        const PairTerms t = momentum_pair<KERN, GH>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
         kahan_add(A.sx, A.cx, t.ax);
         kahan_add(A.sy, A.cy, t.ay);
         kahan_add(A.sz, A.cz, t.az);
@@ -664,7 +739,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
 #ifndef SPH_MOM_MINB
 #define SPH_MOM_MINB 2                  // resident 256-thread CTAs per SM the registers are sized for
 #endif
-template <int TPP, int KERN>
+template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a)
 {
     const float gscale = (float)KernF<KERN>::grad_scale(a.kb, a.kernel_n);
@@ -691,9 +766,9 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
         const uint32_t ci = a.cellxyz[i];
         MomAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (P->zmode)
-            momentum_row<TPP, 1, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
+            momentum_row<TPP, 1, KERN, GH>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
         else
-            momentum_row<TPP, 0, KERN>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
+            momentum_row<TPP, 0, KERN, GH>(a, tab, row, len, G.gl, s_f, sz_f, lz_f, ri, vi, ti, wi5, K, ci, A);
         group_kahan_reduce<TPP>(A.sx, A.cx, G.gmask);
         group_kahan_reduce<TPP>(A.sy, A.cy, G.gmask);
         group_kahan_reduce<TPP>(A.sz, A.cz, G.gmask);
@@ -711,7 +786,7 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
 // ---------------------------------------------------------------------------
 // A7, FP64
 // ---------------------------------------------------------------------------
-template <int TPP, int KERN>
+template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
 {
     if (*a.status & kStBad) return;
@@ -739,7 +814,8 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
             const double r2 = dx * dx + dy * dy + dz * dz;
             const double r = sqrt(r2);
             const double wj = 0.5 * a.f.invh[j];
-            const double F = KernF<KERN>::grad(r, wi, wi5, kn) + KernF<KERN>::grad(r, wj, wj * wj * wj * wj * wj, kn);
+            const double fi = KernF<KERN>::grad(r, wi, wi5, kn), fj = KernF<KERN>::grad(r, wj, wj * wj * wj * wj * wj, kn);
+            const double F = fi + fj;
             const double vx = vxi - a.f.vhx[j], vy = vyi - a.f.vhy[j], vz = vzi - a.f.vhz[j];
             const double vdot = vx * dx + vy * dy + vz * dz;
             double pi_ = 0.0;
@@ -749,12 +825,21 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
                 pi_ = (-a.alpha * 0.5 * (ci + a.f.c[j]) * mu + a.beta * mu * mu) /
                       (0.5 * (rhoi + a.f.rho[j]));
             }
-            const double g = a.s.m[j] * F;
-            const double fa = g * (Ai + a.f.A[j] + pi_);
-            ax += fa * dx;
-            ay += fa * dy;
-            az += fa * dz;
-            du -= g * (Ai + 0.5 * pi_) * vdot;
+            if (GH) {
+                // R20: A holds A/Omega; each side's pressure term with its own kernel
+                const double fa = a.s.m[j] * (2.0 * Ai * fi + 2.0 * a.f.A[j] * fj + pi_ * F);
+                ax += fa * dx;
+                ay += fa * dy;
+                az += fa * dz;
+                du -= a.s.m[j] * (2.0 * Ai * fi + 0.5 * pi_ * F) * vdot;
+            } else {
+                const double g = a.s.m[j] * F;
+                const double fa = g * (Ai + a.f.A[j] + pi_);
+                ax += fa * dx;
+                ay += fa * dy;
+                az += fa * dz;
+                du -= g * (Ai + 0.5 * pi_) * vdot;
+            }
         }
         ax = group_sum<TPP>(ax, G.gmask);
         ay = group_sum<TPP>(ay, G.gmask);
@@ -771,20 +856,26 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
     }
 }
 
-#define SPH_DISPATCH_TPP(KERNEL, KERN, tpp, blocks, L, a)                                   \
-    switch (tpp) {                                                                          \
-    case 1: KERNEL<1, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
-    case 2: KERNEL<2, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
-    case 4: KERNEL<4, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
-    case 16: KERNEL<16, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
-    case 32: KERNEL<32, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
-    default: KERNEL<8, KERN><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;         \
+#define SPH_DISPATCH_TPP(KERNEL, KERN, GH, tpp, blocks, L, a)                                   \
+    switch (tpp) {                                                                              \
+    case 1: KERNEL<1, KERN, GH><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 2: KERNEL<2, KERN, GH><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 4: KERNEL<4, KERN, GH><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;          \
+    case 16: KERNEL<16, KERN, GH><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
+    case 32: KERNEL<32, KERN, GH><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;        \
+    default: KERNEL<8, KERN, GH><<<(unsigned)(blocks), 256, 0, (L).stream>>>(a); break;         \
     }
-#define SPH_DISPATCH(KERNEL, tpp, blocks, L, a)                                             \
-    if ((a).kernel == SPH_KERNEL_SINC) {                                                    \
-        SPH_DISPATCH_TPP(KERNEL, SPH_KERNEL_SINC, tpp, blocks, L, a);                       \
-    } else {                                                                                \
-        SPH_DISPATCH_TPP(KERNEL, SPH_KERNEL_WENDLAND, tpp, blocks, L, a);                   \
+#define SPH_DISPATCH_GH(KERNEL, KERN, tpp, blocks, L, a)                                        \
+    if ((a).grad_h) {                                                                           \
+        SPH_DISPATCH_TPP(KERNEL, KERN, true, tpp, blocks, L, a);                                \
+    } else {                                                                                    \
+        SPH_DISPATCH_TPP(KERNEL, KERN, false, tpp, blocks, L, a);                               \
+    }
+#define SPH_DISPATCH(KERNEL, tpp, blocks, L, a)                                                 \
+    if ((a).kernel == SPH_KERNEL_SINC) {                                                        \
+        SPH_DISPATCH_GH(KERNEL, SPH_KERNEL_SINC, tpp, blocks, L, a);                            \
+    } else {                                                                                    \
+        SPH_DISPATCH_GH(KERNEL, SPH_KERNEL_WENDLAND, tpp, blocks, L, a);                        \
     }
 
 static int64_t pair_blocks(const Launch& L, int64_t n, int tpp)

@@ -24,14 +24,20 @@ _REPORT = {}
 
 @pytest.fixture(scope="session")
 def report():
-    """Measured parity errors; written to gpurun_out/parity_errors.json (when
-    that folder exists) at the end of the session, for the design notes."""
+    """Measured parity errors; merged into the JSON file named by the
+    environment variable SPH_PARITY_REPORT (when set) at the end of the
+    session, for the design notes."""
     return _REPORT
 
 
 def pytest_sessionfinish(session, exitstatus):
-    out = os.path.join(ROOT, "gpurun_out")
-    if _REPORT and os.path.isdir(out):
+    path = os.environ.get("SPH_PARITY_REPORT")
+    if _REPORT and path:
         import json
-        with open(os.path.join(out, "parity_errors.json"), "w") as f:
-            json.dump(_REPORT, f, indent=1, sort_keys=True)
+        old = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                old = json.load(f)
+        old.update(_REPORT)
+        with open(path, "w") as f:
+            json.dump(old, f, indent=1, sort_keys=True)

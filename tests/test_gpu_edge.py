@@ -73,6 +73,19 @@ def test_coincident_pair(B, precision):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grad_h_isolated_particle(B, precision):
+    """A particle with no neighbour inside its support has Omega = 0 in the
+    grad-h form: the density call reports SPH_ENONFINITE."""
+    sim = B.SPH(4, precision=precision, grad_h=1)
+    sim.set_particles(_fields(2, x=np.array([0.1, 0.7])))
+    sim.find_neighbors()
+    with pytest.raises(B.SphError) as e:
+        sim.density()
+    assert e.value.status == B.SPH_ENONFINITE
+    sim.close()
+
+
 def test_overflow_leaves_state(B):
     f = inputs.square_patch(10)
     n = len(f["x"])
@@ -108,7 +121,8 @@ def test_bad_inputs(B):
 
 @pytest.mark.parametrize("kw", [dict(cell_factor=0.3), dict(threads_per_particle=3),
                                 dict(max_particles=0), dict(gamma=1.0), dict(max_patches=300),
-                                dict(kernel=2), dict(kernel=1, kernel_n=1), dict(kernel=1, kernel_n=17)])
+                                dict(kernel=2), dict(kernel=1, kernel_n=1), dict(kernel=1, kernel_n=17),
+                                dict(grad_h=2), dict(grad_h=-1)])
 def test_bad_config(B, kw):
     mp = kw.pop("max_particles", 8)
     with pytest.raises(B.SphError) as e:

@@ -228,6 +228,61 @@ def test_sinc_kernel_ten_steps(B, orc, precision, tol, report):
     sim.close()
 
 
+def _oracle_forces_gradh(orc, f, lz=1.0):
+    nb = orc.neighbors(f["x"], f["y"], f["z"], f["h"], lz)
+    rho = orc.density(f["x"], f["y"], f["z"], f["m"], f["h"], nb, lz)
+    P, c = orc.eos(rho, f["u"])
+    om = orc.omega(f["x"], f["y"], f["z"], f["m"], f["h"], rho, nb, lz)
+    ax, ay, az, du, sa, sdu = orc.momentum_energy(f["x"], f["y"], f["z"], f["vx"], f["vy"], f["vz"],
+                                                  f["m"], f["h"], rho, P, c, nb, lz, omega=om)
+    return dict(rho=rho, P=P, c=c, ax=ax, ay=ay, az=az, du=du, sa=sa, sdu=sdu), om
+
+
+# The oracle takes Omega = 1 + h/(3 rho) sum m dW/dh as written: a sum near
+# -1 added to 1, so its own rounding error in Omega is a few ulp of 1, i.e.
+# relative few eps / Omega.  The GPU path sums the non-negative terms of the
+# same quantity (no cancellation).  Where the inputs make Omega small (the
+# random cloud with h drawn apart from the density: Omega down to 1.5e-6 for
+# the Sinc kernel) the comparison allows for the oracle's error.
+ORACLE_OMEGA_ULPS = 64
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+@pytest.mark.parametrize("case", ["patch20", "cloud_av", "irregular", "htail_near", "zwrap"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_grad_h_pair_sums(B, orc, kernel, case, precision, tol, report):
+    """The grad-h momentum and energy form (Omega from the dW/dh sum over the
+    same neighbours as the density) against the oracle's."""
+    f = FORCE_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    g = _gpu_forces(B, f, precision, lz=lz, kernel=kernel, kernel_n=6, grad_h=1)
+    with orc.kernel(kernel, 6):
+        o, om = _oracle_forces_gradh(orc, f, lz)
+    assert om.min() > 0.0
+    tol_eff = tol + ORACLE_OMEGA_ULPS * np.finfo(np.float64).eps / om.min()
+    _check_forces(g, o, tol_eff, report, "gradh/%s/%s/%s" % (kernel, precision, case))
+    report["gradh/%s/%s/%s" % (kernel, precision, case)]["omega_min"] = float(om.min())
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "sinc"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+def test_grad_h_ten_steps(B, orc, kernel, precision, tol, report):
+    f = inputs.square_patch(20)
+    sim = B.SPH(len(f["x"]), precision=precision, kernel=kernel, kernel_n=6, grad_h=1)
+    sim.set_particles(f)
+    ref = orc.Sim(f, kernel=kernel, kernel_n=6, grad_h=True)
+    hist = []
+    for step in range(10):
+        dt = sim.step(1)
+        ref.step(1)
+        assert abs(dt - ref.dt) <= tol * ref.dt, (step, dt, ref.dt)
+        g = {k: sim.field(k) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "nown", "rho",
+                                       "ax", "ay", "az")}
+        hist.append(_compare_state(g, ref, tol, "grad-h step %d" % step))
+    report["gradh_steps10/%s/%s" % (kernel, precision)] = hist
+    sim.close()
+
+
 def _compare_state(g, o, tol, what):
     errs = {k: normwise(g[k], o[k]) for k in ("x", "y", "u", "h", "rho")}
     errs["v"] = normwise_vec([g["vx"], g["vy"], g["vz"]], [o["vx"], o["vy"], o["vz"]])
