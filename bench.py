@@ -226,6 +226,11 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel", default="wendland", choices=["wendland", "sinc"],
                     help="SPH kernel of Sec. 3 (Sinc with n = 6)")
+    ap.add_argument("--pair-mode", default="auto", choices=["auto", "lists", "fused"],
+                    help="pair sums over neighbour lists, list-free (the search inside the sums), "
+                         "or whichever the autotuner finds faster")
+    ap.add_argument("--mode-steps", type=int, default=10,
+                    help="steps timed for the pair mode not chosen (0: skip)")
     ap.add_argument("--grad-h", action="store_true",
                     help="the grad-h momentum and energy form (Omega factors)")
     ap.add_argument("--cell-factor", type=float, default=0.0,
@@ -257,12 +262,13 @@ def main():
     stream = torch.cuda.current_stream()
     dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
 
-    def make(precision, graph=False):
-        kw = {"kernel": args.kernel, "kernel_n": 6, "grad_h": int(args.grad_h)}
+    def make(precision, graph=False, **over):
+        kw = {"kernel": args.kernel, "kernel_n": 6, "grad_h": int(args.grad_h), "pair_mode": args.pair_mode}
         if args.cell_factor:
             kw["cell_factor"] = args.cell_factor
         if args.tpp:
             kw["threads_per_particle"] = args.tpp
+        kw.update(over)
         sim = binding.SPH(n, precision=precision, stream=stream.cuda_stream,
                           use_graph=int(graph), max_pairs=int(160 * n), **kw)
         sim.set_particles(dfields)
@@ -280,6 +286,7 @@ def main():
         sim.autotune()
         sim.step(1)
     tpp, cf = binding.sph_get_tuning(sim.ctx)
+    mode = sim.pair_mode()
     torch.cuda.synchronize()
     sim.pair_count(reset=True)
     # the timed region runs the phases with CUDA events between them (per-kernel
@@ -339,28 +346,40 @@ def main():
     peaks, peak_src = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or SM_MAX_MHZ
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    # dominant kernel: the neighbour-list search (k_nb_thread), HBM roofline
-    # on its algorithmic bytes
-    nb_ms = prof["nb"][0] / max(args.steps, 1)
-    nb_bytes = NB_BYTES_PER_ENTRY * pairs_per_step + NB_BYTES_PER_PARTICLE * n
-    nb_gbs = nb_bytes / (nb_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_nb_thread", "achieved": nb_gbs, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": nb_gbs / peaks["hbm_gbs"],
-            "traffic": (NB_DRAM_BYTES_PER_ENTRY * pairs_per_step) if NB_DRAM_BYTES_PER_ENTRY else None,
-            "algorithmic_bytes": nb_bytes, "ms_per_launch": nb_ms,
-            "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src,
-            "share_of_step": prof["nb"][0] / ms_total}
-    # the pair sums: FP32 pipe (mixed) against the derived FP32 peak
     mom_ms = prof["momentum"][0] / max(args.steps, 1)
     flops_pair = {(False, False): FLOPS_PER_PAIR_MOMENTUM, (True, False): FLOPS_PER_PAIR_MOMENTUM_SINC,
                   (False, True): FLOPS_PER_PAIR_MOMENTUM_GRADH,
                   (True, True): FLOPS_PER_PAIR_MOMENTUM_SINC_GRADH}[(args.kernel == "sinc", args.grad_h)]
     mom_tf = flops_pair * pairs_per_step / (mom_ms / 1e3) / 1e12
-    roof_mom = {"bound": "alu", "kernel": "k_momentum_mixed" if args.precision == "mixed" else "k_momentum_fp64",
+    prec_tag = "mixed" if args.precision == "mixed" else "fp64"
+    if mode == "lists":
+        # dominant kernel: the neighbour-list search (k_nb_thread), HBM roofline
+        # on its algorithmic bytes
+        nb_ms = prof["nb"][0] / max(args.steps, 1)
+        nb_bytes = NB_BYTES_PER_ENTRY * pairs_per_step + NB_BYTES_PER_PARTICLE * n
+        nb_gbs = nb_bytes / (nb_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_nb_thread", "achieved": nb_gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": nb_gbs / peaks["hbm_gbs"],
+                "traffic": (NB_DRAM_BYTES_PER_ENTRY * pairs_per_step) if NB_DRAM_BYTES_PER_ENTRY else None,
+                "algorithmic_bytes": nb_bytes, "ms_per_launch": nb_ms,
+                "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src,
+                "share_of_step": prof["nb"][0] / ms_total}
+    else:
+        # list-free: the momentum pass (search + pair sums) dominates; its pair
+        # arithmetic against the FP32 peak (the search is not counted)
+        roof = {"bound": "alu", "kernel": "k_fused_momentum_" + prec_tag, "achieved": mom_tf,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak, "traffic": None,
+                "flops_per_pair": flops_pair, "ms_per_launch": mom_ms,
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
+                               % (SMS, FP32_LANES_PER_SM, sm_max),
+                "share_of_step": prof["momentum"][0] / ms_total}
+    # the pair sums: FP32 pipe (mixed) against the derived FP32 peak
+    roof_mom = {"bound": "alu", "kernel": ("k_momentum_" if mode == "lists" else "k_fused_momentum_") + prec_tag,
                 "achieved": mom_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak,
                 # the DRAM figure is the standard Wendland variant's
                 "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step)
-                if MOMENTUM_DRAM_BYTES_PER_ENTRY and args.kernel == "wendland" and not args.grad_h else None,
+                if MOMENTUM_DRAM_BYTES_PER_ENTRY and args.kernel == "wendland" and not args.grad_h
+                and mode == "lists" else None,
                 "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
                                % (SMS, FP32_LANES_PER_SM, sm_max),
                 "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf / fma_peak,
@@ -381,7 +400,7 @@ def main():
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
-                   "threads_per_particle": tpp, "cell_factor": cf,
+                   "threads_per_particle": tpp, "cell_factor": cf, "pair_mode": mode,
                    "timed": "K steps with CUDA events between phases (no graph)"},
         "steps_per_s": steps_per_s, "pairs_per_step": pairs_per_step,
         "gpu_launches": launches, "clocks": clk,
@@ -391,6 +410,35 @@ def main():
                          "ms_per_step": ms_graph / args.steps, "steps_per_s": 1e3 * args.steps / ms_graph,
                          "steps": args.steps},
     }
+
+    # the other pair mode at the same cell factor (and lanes per particle)
+    if args.mode_steps > 0 and world == 1:
+        other = "fused" if mode == "lists" else "lists"
+        sim.close()
+        so = make(args.precision, pair_mode=other, cell_factor=cf, threads_per_particle=tpp)
+        for _ in range(args.warmup):
+            so.step(1)
+        torch.cuda.synchronize()
+        so.pair_count(reset=True)
+        so.profile(True)
+        so.profile()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.mode_steps):
+            so.step(1)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        mso = b0.elapsed_time(b1) / args.mode_steps
+        po = so.pair_count(reset=True) / args.mode_steps
+        profo = so.profile()
+        so.profile(False)
+        so.close()
+        line["other_pair_mode"] = {"pair_mode": other, "value": 2.0 * po / (mso / 1e3), "unit": UNIT,
+                                   "ms_per_step": mso, "steps": args.mode_steps, "cell_factor": cf,
+                                   "threads_per_particle": tpp,
+                                   "phase_ms_per_step": {k: v[0] / args.mode_steps for k, v in profo.items()}}
+        sim = make(args.precision, pair_mode=mode, cell_factor=cf, threads_per_particle=tpp)
 
     # FP64 GPU path on the same patch
     if args.fp64_steps > 0 and args.precision == "mixed":

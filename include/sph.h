@@ -58,6 +58,17 @@ typedef enum {
 enum { SPH_FP64 = 0, SPH_MIXED = 1 };               /* sph_config.precision */
 enum { SPH_KERNEL_WENDLAND = 0, SPH_KERNEL_SINC = 1 }; /* sph_config.kernel */
 
+/* How the pair sums find their pairs (sph_config.pair_mode). */
+enum {
+    SPH_PAIRS_LISTS = 0,    /* the step writes neighbour lists (A4) and the
+                               density and momentum sums read them */
+    SPH_PAIRS_FUSED = 1,    /* no lists: the density and the momentum sums each
+                               run the neighbour search themselves and take
+                               the same pairs in the same order */
+    SPH_PAIRS_AUTO = 2      /* SPH_PAIRS_LISTS until sph_autotune, which times
+                               both and keeps the faster */
+};
+
 /* Fields for sph_get_field (all returned as double, original order). */
 enum {
     SPH_FIELD_X = 0, SPH_FIELD_Y, SPH_FIELD_Z,
@@ -97,6 +108,7 @@ typedef struct {
                                fails the step with SPH_ENONFINITE;
                                0 (default): the symmetrised-kernel form */
     int32_t threads_per_particle; /* 0 = auto; else 1, 2, 4, 8, 16 or 32 */
+    int32_t pair_mode;      /* SPH_PAIRS_LISTS (default), _FUSED or _AUTO */
     double cell_factor;     /* cell edge = 2 h_s * cell_factor, in [1/3, 4]
                                (h_s: the patch's class threshold of h) */
     int64_t max_particles;  /* capacity, <= 2^25 */
@@ -170,7 +182,9 @@ sph_status sph_copy_neighbors(sph_ctx* ctx, uint64_t* off, uint32_t* col, uint32
 
 /* Density summation rho_i = m_i W(0,h_i) + sum_j m_j W(r_ij, h_i) (Sec. 3,
  * Eq. 2) and the ideal-gas EOS P = (gamma-1) rho u, c = sqrt(gamma P/rho), on
- * the current neighbour lists.  Errors: SPH_ESTATE (no lists),
+ * the current neighbour lists, or (SPH_PAIRS_FUSED in effect) over the
+ * neighbour search itself, which then also sets |N(i)| and n_i.  Needs
+ * sph_find_neighbors on the current particles.  Errors: SPH_ESTATE,
  * SPH_ENONFINITE. */
 sph_status sph_density(sph_ctx* ctx);
 
@@ -209,12 +223,17 @@ sph_status sph_get_state(sph_ctx* ctx, void* buf, size_t* bytes);
 sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes);
 
 /* Times the neighbour and pair-sum phases for a few candidate launch
- * configurations (threads per particle, cell factor) on the current
+ * configurations (threads per particle, cell factor and, with
+ * SPH_PAIRS_AUTO, lists against the list-free sums) on the current
  * particles and keeps the fastest; the particle state is left unchanged. */
 sph_status sph_autotune(sph_ctx* ctx);
 
 /* Current launch configuration (after sph_autotune or as configured). */
 sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* cell_factor);
+
+/* The pair mode in effect: SPH_PAIRS_LISTS or SPH_PAIRS_FUSED (SPH_PAIRS_AUTO
+ * resolves to one of them in sph_autotune). */
+sph_status sph_get_pair_mode(sph_ctx* ctx, int32_t* mode);
 
 /* Phase timers: when enabled, every phase of sph_step/sph_find_neighbors/
  * sph_density/sph_momentum_energy is bracketed by CUDA events on the

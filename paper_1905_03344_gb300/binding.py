@@ -19,6 +19,8 @@ from . import build as _build
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EOVERFLOW, SPH_ENONFINITE, SPH_ETIMEOUT, SPH_ESTATE = range(8)
 SPH_FP64, SPH_MIXED = 0, 1
 SPH_KERNEL_WENDLAND, SPH_KERNEL_SINC = 0, 1
+SPH_PAIRS_LISTS, SPH_PAIRS_FUSED, SPH_PAIRS_AUTO = 0, 1, 2
+PAIR_MODES = {"lists": SPH_PAIRS_LISTS, "fused": SPH_PAIRS_FUSED, "auto": SPH_PAIRS_AUTO}
 
 FIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "h", "u", "du_prev", "axp", "ayp", "azp",
           "rho", "P", "c", "ax", "ay", "az", "du", "nown", "nnb"]
@@ -33,7 +35,8 @@ class SphConfig(ctypes.Structure):
                 ("av_alpha", ctypes.c_double), ("av_beta", ctypes.c_double),
                 ("av_eps", ctypes.c_double), ("lz", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("adapt_h", ctypes.c_int32), ("grad_h", ctypes.c_int32),
-                ("threads_per_particle", ctypes.c_int32), ("cell_factor", ctypes.c_double),
+                ("threads_per_particle", ctypes.c_int32), ("pair_mode", ctypes.c_int32),
+                ("cell_factor", ctypes.c_double),
                 ("max_particles", ctypes.c_int64), ("max_pairs", ctypes.c_int64),
                 ("max_patches", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p)]
@@ -75,6 +78,7 @@ SIGNATURES = {
     "sph_set_state": (_ST, [_P, _P, ctypes.c_size_t]),
     "sph_autotune": (_ST, [_P]),
     "sph_get_tuning": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
+    "sph_get_pair_mode": (_ST, [_P, ctypes.POINTER(_I32)]),
     "sph_set_profiling": (_ST, [_P, ctypes.c_int]),
     "sph_get_profile": (_ST, [_P, _P, _P, _I32]),
     "sph_get_launch_count": (_ST, [_P, ctypes.POINTER(_I64)]),
@@ -270,6 +274,13 @@ def sph_autotune(ctx):
     _check(ctx, lib().sph_autotune(ctx))
 
 
+def sph_get_pair_mode(ctx):
+    """"lists" or "fused": how the pair sums currently find their pairs."""
+    m = ctypes.c_int32()
+    _check(ctx, lib().sph_get_pair_mode(ctx, ctypes.byref(m)))
+    return "fused" if m.value == SPH_PAIRS_FUSED else "lists"
+
+
 def sph_get_tuning(ctx):
     t, f = ctypes.c_int32(), ctypes.c_double()
     _check(ctx, lib().sph_get_tuning(ctx, ctypes.byref(t), ctypes.byref(f)))
@@ -343,6 +354,8 @@ class SPH:
         cfg.precision = SPH_FP64 if precision == "fp64" else SPH_MIXED
         if isinstance(kw.get("kernel"), str):
             kw["kernel"] = {"wendland": SPH_KERNEL_WENDLAND, "sinc": SPH_KERNEL_SINC}[kw["kernel"]]
+        if isinstance(kw.get("pair_mode"), str):
+            kw["pair_mode"] = PAIR_MODES[kw["pair_mode"]]
         cfg.max_particles = int(max_particles)
         cfg.max_patches = int(max_patches)
         if stream is not None:
@@ -408,6 +421,9 @@ class SPH:
     def autotune(self):
         sph_autotune(self.ctx)
         return sph_get_tuning(self.ctx)
+
+    def pair_mode(self):
+        return sph_get_pair_mode(self.ctx)
 
     def profile(self, enable=None):
         if enable is not None:

@@ -13,9 +13,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsph_gb300.so")
-SOURCES = ["sph_sort.cu", "sph_neighbors.cu", "sph_pairs.cu", "sph_step.cu", "sph_api.cu", "sph_noalloc.cu",
-           "sph_peak.cu"]
-HEADERS = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(ROOT, "include", "sph.h")]
+SOURCES = ["sph_sort.cu", "sph_neighbors.cu", "sph_pairs.cu", "sph_fused_density.cu", "sph_fused_momentum.cu",
+           "sph_step.cu", "sph_api.cu", "sph_noalloc.cu", "sph_peak.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("sph_internal.cuh", "sph_walk.cuh", "sph_pairmath.cuh", "sph_fused.cuh")] + [
+    os.path.join(ROOT, "include", "sph.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -74,6 +74,7 @@ struct sph_ctx {
     int tpp_pair = 8;
     double cell_factor = 0.5;
     int mixed = 1;
+    bool fused = false;            // pair sums without lists (SPH_PAIRS_FUSED in effect)
 
     State st[2];
     int cur = 0;
@@ -379,6 +380,19 @@ void enqueue_lists(sph_ctx* ctx)
 
 void enqueue_density(sph_ctx* ctx)
 {
+    if (ctx->fused) {
+        {
+            // the density pass counts the pairs again
+            Phase p(ctx, SPH_PHASE_NB_RESET);
+            cudaMemsetAsync(ctx->pool_used + 1, 0, sizeof(unsigned long long), ctx->stream);
+        }
+        Phase p(ctx, SPH_PHASE_DENSITY);
+        ctx->launches += launch_fused_density(launch_of(ctx), nb_args(ctx), pair_args(ctx),
+                                              stencil_k(ctx->cell_factor), ctx->mixed);
+        // cnt now holds the row lengths of the current order: hints for the next sort
+        cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
+        return;
+    }
     Phase p(ctx, SPH_PHASE_DENSITY);
     ctx->launches += launch_density(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
 }
@@ -386,13 +400,17 @@ void enqueue_density(sph_ctx* ctx)
 void enqueue_momentum(sph_ctx* ctx)
 {
     Phase p(ctx, SPH_PHASE_MOMENTUM);
-    ctx->launches += launch_momentum(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
+    if (ctx->fused)
+        ctx->launches += launch_fused_momentum(launch_of(ctx), nb_args(ctx), pair_args(ctx),
+                                               stencil_k(ctx->cell_factor), ctx->mixed);
+    else
+        ctx->launches += launch_momentum(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
 }
 
 void enqueue_step(sph_ctx* ctx)
 {
     enqueue_sort(ctx);
-    enqueue_lists(ctx);
+    if (!ctx->fused) enqueue_lists(ctx);
     enqueue_density(ctx);
     const Launch L = launch_of(ctx);
     {
@@ -601,6 +619,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     if (cfg.kernel == SPH_KERNEL_SINC && !(cfg.kernel_n >= 2 && cfg.kernel_n <= 16))
         return fail(nullptr, SPH_EINVAL, "kernel_n must be in [2, 16] for the Sinc kernel");
     if (cfg.grad_h != 0 && cfg.grad_h != 1) return fail(nullptr, SPH_EINVAL, "grad_h must be 0 or 1");
+    if (cfg.pair_mode != SPH_PAIRS_LISTS && cfg.pair_mode != SPH_PAIRS_FUSED && cfg.pair_mode != SPH_PAIRS_AUTO)
+        return fail(nullptr, SPH_EINVAL, "pair_mode must be SPH_PAIRS_LISTS, SPH_PAIRS_FUSED or SPH_PAIRS_AUTO");
     if (cfg.max_particles < 1 || cfg.max_particles > kMaxParticles)
         return fail(nullptr, SPH_EINVAL, "max_particles must be in [1, 2^25]");
     if (cfg.max_patches < 1 || cfg.max_patches > kMaxPatches)
@@ -642,6 +662,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ctx->kernel_b = kernel_norm(cfg.kernel, cfg.kernel_n);
     ctx->cell_factor = cfg.cell_factor;
     if (t) ctx->tpp_pair = t;
+    ctx->fused = cfg.pair_mode == SPH_PAIRS_FUSED;
     ctx->cap_n = cfg.max_particles;
     ctx->cap_patch = cfg.max_patches;
     ctx->max_pairs = cfg.max_pairs > 0 ? cfg.max_pairs : 160 * cfg.max_particles;
@@ -843,7 +864,8 @@ sph_status sph_density(sph_ctx* ctx)
 {
     sph_status st = begin_call(ctx);
     if (st != SPH_OK) return st;
-    if (!ctx->nb_valid) return fail(ctx, SPH_ESTATE, "sph_density needs current neighbour lists");
+    if (!ctx->nb_valid)
+        return fail(ctx, SPH_ESTATE, "sph_density needs sph_find_neighbors on the current particles");
     enqueue_density(ctx);
     st = after_launches(ctx, "sph_density");
     if (st != SPH_OK) return st;
@@ -1134,30 +1156,49 @@ sph_status sph_autotune(sph_ctx* ctx)
         }
         return best;
     };
+    // lists: the search writing them plus the best lanes-per-particle of the
+    // sums over them; list-free: the two passes (each runs the search)
+    const bool try_lists = ctx->cfg.pair_mode != SPH_PAIRS_FUSED;
+    const bool try_fused = ctx->cfg.pair_mode != SPH_PAIRS_LISTS;
     double best_total = 1e300, best_f = ctx->cell_factor;
     int best_pair = ctx->tpp_pair;
+    bool best_fused = ctx->fused;
     for (double f : factors) {
         ctx->cell_factor = f;
         enqueue_sort(ctx);
-        float bpair = 1e30f;
-        int tpair = 8;
-        const float bnb = timeit([&] { enqueue_lists(ctx); });
-        for (int t : pair_tpps) {
-            ctx->tpp_pair = t;
-            float ms = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
-            if (ms < bpair) { bpair = ms; tpair = t; }
+        if (try_lists) {
+            ctx->fused = false;
+            float bpair = 1e30f;
+            int tpair = 8;
+            const float bnb = timeit([&] { enqueue_lists(ctx); });
+            for (int t : pair_tpps) {
+                ctx->tpp_pair = t;
+                float ms = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
+                if (ms < bpair) { bpair = ms; tpair = t; }
+            }
+            const double tot = (double)bnb + (double)bpair;
+            if (tot < best_total) {
+                best_total = tot;
+                best_f = f;
+                best_pair = tpair;
+                best_fused = false;
+            }
         }
-        const double tot = (double)bnb + (double)bpair;
-        if (tot < best_total) {
-            best_total = tot;
-            best_f = f;
-            best_pair = tpair;
+        if (try_fused) {
+            ctx->fused = true;
+            const double tot = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
+            if (tot < best_total) {
+                best_total = tot;
+                best_f = f;
+                best_fused = true;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->cell_factor = best_f;
     ctx->tpp_pair = best_pair;
+    ctx->fused = best_fused;
     ctx->prof = prof0;
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
     st = after_launches(ctx, "sph_autotune");
@@ -1170,6 +1211,13 @@ sph_status sph_get_tuning(sph_ctx* ctx, int32_t* tpp, double* cell_factor)
     if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
     if (tpp) *tpp = ctx->tpp_pair;
     if (cell_factor) *cell_factor = ctx->cell_factor;
+    return SPH_OK;
+}
+
+sph_status sph_get_pair_mode(sph_ctx* ctx, int32_t* mode)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "ctx is NULL");
+    if (mode) *mode = ctx->fused ? SPH_PAIRS_FUSED : SPH_PAIRS_LISTS;
     return SPH_OK;
 }
 

@@ -245,6 +245,11 @@ struct PairArgs {
 };
 int launch_density(const Launch& L, const PairArgs& a, int tpp, int mixed);
 int launch_momentum(const Launch& L, const PairArgs& a, int tpp, int mixed);
+// list-free pair sums over the search of the current grid (stencil
+// half-extent K); the density pass also writes |N(i)| and n_i and adds the
+// pairs to pool_used[1]
+int launch_fused_density(const Launch& L, const NbArgs& a, const PairArgs& pa, int K, int mixed);
+int launch_fused_momentum(const Launch& L, const NbArgs& a, const PairArgs& pa, int K, int mixed);
 
 struct StepArgs {
     int64_t n;

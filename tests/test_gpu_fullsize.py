@@ -149,3 +149,24 @@ def test_batched_64_patches(B, orc, report):
         assert abs(dts[p] - ref.dt) <= 1e-12 * ref.dt, (p, dts[p], ref.dt)
         assert np.abs(x[a:b] - ref["x"]).max() <= 1e-12 * max(1.0, np.abs(ref["x"]).max()), p
         assert np.abs(hh[a:b] - ref["h"]).max() <= 1e-12 * np.abs(ref["h"]).max(), p
+
+
+def test_full_size_fused_matches_lists(B):
+    """The 200^3 patch in the list-free mode at the benchmark's cell factor:
+    every force field, |N(i)| and n_i the same bits as the lists with one lane
+    per particle."""
+    f = inputs.config_patch("c3")
+    n = len(f["x"])
+    out = {}
+    keys = ("rho", "P", "c", "ax", "ay", "az", "du", "nnb", "nown")
+    for mode in ("fused", "lists"):
+        sim = B.SPH(n, precision="mixed", max_pairs=160 * n, pair_mode=mode, threads_per_particle=1,
+                    cell_factor=0.5)
+        sim.set_particles(f)
+        sim.find_neighbors()
+        sim.density()
+        sim.momentum_energy()
+        out[mode] = {k: sim.field(k) for k in keys}
+        sim.close()
+    for k in keys:
+        assert np.array_equal(out["fused"][k].view(np.uint64), out["lists"][k].view(np.uint64)), k
