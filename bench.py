@@ -229,6 +229,9 @@ def main():
     ap.add_argument("--pair-mode", default="auto", choices=["auto", "lists", "fused"],
                     help="pair sums over neighbour lists, list-free (the search inside the sums), "
                          "or whichever the autotuner finds faster")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="reuse the neighbour search across steps: search radius scaled by 1 + skin, "
+                         "exact lists filtered from it every step (0: search every step)")
     ap.add_argument("--mode-steps", type=int, default=10,
                     help="steps timed for the pair mode not chosen (0: skip)")
     ap.add_argument("--grad-h", action="store_true",
@@ -263,7 +266,8 @@ def main():
     dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
 
     def make(precision, graph=False, **over):
-        kw = {"kernel": args.kernel, "kernel_n": 6, "grad_h": int(args.grad_h), "pair_mode": args.pair_mode}
+        kw = {"kernel": args.kernel, "kernel_n": 6, "grad_h": int(args.grad_h), "pair_mode": args.pair_mode,
+              "list_skin": args.skin}
         if args.cell_factor:
             kw["cell_factor"] = args.cell_factor
         if args.tpp:
@@ -295,6 +299,7 @@ def main():
     sim.profile()      # reset accumulators
     clocks = Clocks(local)
     l0 = sim.launches()
+    rb0 = sim.list_rebuilds()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -311,6 +316,7 @@ def main():
         torch.distributed.barrier()
     ms_total = e0.elapsed_time(e1)
     launches = sim.launches() - l0
+    rebuilds = sim.list_rebuilds() - rb0
     pairs = sim.pair_count(reset=True)
     prof = sim.profile()
     sim.profile(False)
@@ -401,6 +407,7 @@ def main():
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
                    "threads_per_particle": tpp, "cell_factor": cf, "pair_mode": mode,
+                   "list_skin": args.skin, "searches_in_timed_steps": rebuilds if args.skin > 0 else args.steps,
                    "timed": "K steps with CUDA events between phases (no graph)"},
         "steps_per_s": steps_per_s, "pairs_per_step": pairs_per_step,
         "gpu_launches": launches, "clocks": clk,

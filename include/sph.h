@@ -111,6 +111,21 @@ typedef struct {
     int32_t pair_mode;      /* SPH_PAIRS_LISTS (default), _FUSED or _AUTO */
     double cell_factor;     /* cell edge = 2 h_s * cell_factor, in [1/3, 4]
                                (h_s: the patch's class threshold of h) */
+    double list_skin;       /* 0 (default): every step sorts and searches.
+                               skin > 0 (at most 1; list mode only): the search
+                               lists the candidate superset r < 2 (1 + skin)
+                               max(h_i, h_j), and each step takes its exact
+                               lists from that superset with the same
+                               predicate as the search; the sort and search
+                               run again only once some particle has moved
+                               farther than min_k ((1 + skin) h_k0 - h_k)
+                               since the superset was built (h_k0: h then),
+                               which keeps every pair in the superset.  The
+                               lists are the same sets; within a row the
+                               order is the superset's.  sph_find_neighbors
+                               also takes a superset that still holds (no
+                               sort then); a state restored by sph_set_state
+                               rebuilds at its first step. */
     int64_t max_particles;  /* capacity, <= 2^25 */
     int64_t max_pairs;      /* neighbour-list capacity (total list entries);
                                0 = 160 * max_particles.  The list pool holds
@@ -234,6 +249,10 @@ sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* c
 /* The pair mode in effect: SPH_PAIRS_LISTS or SPH_PAIRS_FUSED (SPH_PAIRS_AUTO
  * resolves to one of them in sph_autotune). */
 sph_status sph_get_pair_mode(sph_ctx* ctx, int32_t* mode);
+
+/* Candidate supersets built so far (list_skin > 0: sph_find_neighbors and
+ * the steps that had to sort and search again). */
+sph_status sph_get_list_rebuilds(sph_ctx* ctx, int64_t* n);
 
 /* Phase timers: when enabled, every phase of sph_step/sph_find_neighbors/
  * sph_density/sph_momentum_energy is bracketed by CUDA events on the

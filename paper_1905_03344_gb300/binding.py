@@ -36,7 +36,7 @@ class SphConfig(ctypes.Structure):
                 ("av_eps", ctypes.c_double), ("lz", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("adapt_h", ctypes.c_int32), ("grad_h", ctypes.c_int32),
                 ("threads_per_particle", ctypes.c_int32), ("pair_mode", ctypes.c_int32),
-                ("cell_factor", ctypes.c_double),
+                ("cell_factor", ctypes.c_double), ("list_skin", ctypes.c_double),
                 ("max_particles", ctypes.c_int64), ("max_pairs", ctypes.c_int64),
                 ("max_patches", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p)]
@@ -79,6 +79,7 @@ SIGNATURES = {
     "sph_autotune": (_ST, [_P]),
     "sph_get_tuning": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
     "sph_get_pair_mode": (_ST, [_P, ctypes.POINTER(_I32)]),
+    "sph_get_list_rebuilds": (_ST, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "sph_set_profiling": (_ST, [_P, ctypes.c_int]),
     "sph_get_profile": (_ST, [_P, _P, _P, _I32]),
     "sph_get_launch_count": (_ST, [_P, ctypes.POINTER(_I64)]),
@@ -281,6 +282,13 @@ def sph_get_pair_mode(ctx):
     return "fused" if m.value == SPH_PAIRS_FUSED else "lists"
 
 
+def sph_get_list_rebuilds(ctx):
+    """Candidate supersets built so far (list_skin > 0)."""
+    v = ctypes.c_int64()
+    _check(ctx, lib().sph_get_list_rebuilds(ctx, ctypes.byref(v)))
+    return v.value
+
+
 def sph_get_tuning(ctx):
     t, f = ctypes.c_int32(), ctypes.c_double()
     _check(ctx, lib().sph_get_tuning(ctx, ctypes.byref(t), ctypes.byref(f)))
@@ -424,6 +432,9 @@ class SPH:
 
     def pair_mode(self):
         return sph_get_pair_mode(self.ctx)
+
+    def list_rebuilds(self):
+        return sph_get_list_rebuilds(self.ctx)
 
     def profile(self, enable=None):
         if enable is not None:

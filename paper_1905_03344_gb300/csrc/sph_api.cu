@@ -75,6 +75,18 @@ struct sph_ctx {
     double cell_factor = 0.5;
     int mixed = 1;
     bool fused = false;            // pair sums without lists (SPH_PAIRS_FUSED in effect)
+    // reused candidate supersets (list_skin > 0, list mode)
+    double skin = 0.0;
+    bool sup_valid = false;        // the superset of the current order still holds every pair
+    uint32_t *col_s = nullptr, *cnt_s = nullptr;  // superset pool and row lengths (rows at rowstart)
+    int* hint_ok_s = nullptr;      // device flag: cnt_s holds row lengths of the current order
+    int64_t max_pairs_s = 0;
+    SkinRef skinref{};
+    double* hsearch_pre = nullptr; // search h of a superset build, order before its sort
+    unsigned long long* skin_red = nullptr;
+    int* skin_flag = nullptr;
+    int* h_skin_flag = nullptr;    // pinned
+    int64_t rebuilds = 0;          // superset builds so far
 
     State st[2];
     int cur = 0;
@@ -117,8 +129,10 @@ struct sph_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
     int64_t launches = 0;
 
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int64_t graph_kernels[2] = {0, 0};
+    // captured steps by buffer parity and kind (1: with the sort and search,
+    // 0: on a reused superset)
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t graph_kernels[2][2] = {{0, 0}, {0, 0}};
 
     std::vector<void*> allocs;
 };
@@ -168,11 +182,12 @@ Launch launch_of(const sph_ctx* ctx) { return Launch{ctx->stream, ctx->sms}; }
 
 void destroy_graphs(sph_ctx* ctx)
 {
-    for (int k = 0; k < 2; k++) {
-        if (ctx->gexec[k]) cudaGraphExecDestroy(ctx->gexec[k]);
-        ctx->gexec[k] = nullptr;
-        ctx->graph_kernels[k] = 0;
-    }
+    for (int k = 0; k < 2; k++)
+        for (int r = 0; r < 2; r++) {
+            if (ctx->gexec[k][r]) cudaGraphExecDestroy(ctx->gexec[k][r]);
+            ctx->gexec[k][r] = nullptr;
+            ctx->graph_kernels[k][r] = 0;
+        }
 }
 
 // ---- phase timers -----------------------------------------------------------
@@ -329,19 +344,29 @@ StepArgs step_args(sph_ctx* ctx)
 }
 
 // ---- the phases (asynchronous, no host synchronisation) -----------------------
-void enqueue_sort(sph_ctx* ctx)
+// superset: the sort and cells of a candidate superset (reused lists): the
+// search h of every particle grown by its skin, gathered into skinref.h0;
+// the row-length hints come from the superset's rows
+void enqueue_sort(sph_ctx* ctx, bool superset = false)
 {
     const Launch L = launch_of(ctx);
+    State s = ctx->st[ctx->cur];
+    if (superset) {
+        const bool have_n = !ctx->fresh && ctx->cfg.adapt_h;
+        ctx->launches += launch_skin_radius(L, ctx->n, ctx->st[ctx->cur], have_n ? ctx->nown : nullptr, ctx->hfac,
+                                            ctx->cfg.n_target, ctx->skin, ctx->hsearch_pre);
+        s.h = ctx->hsearch_pre;
+    }
     {
         Phase p(ctx, SPH_PHASE_BBOX);
         ctx->launches += launch_reset_red(L, ctx->npatch, ctx->red);
-        ctx->launches += launch_reduce_bbox(L, ctx->st[ctx->cur], ctx->items, ctx->nitems, ctx->red);
-        ctx->launches += launch_h_hist(L, ctx->st[ctx->cur], ctx->items, ctx->nitems, ctx->red);
+        ctx->launches += launch_reduce_bbox(L, s, ctx->items, ctx->nitems, ctx->red);
+        ctx->launches += launch_h_hist(L, s, ctx->items, ctx->nitems, ctx->red);
         ctx->launches += launch_grid_params(L, ctx->npatch, ctx->red, ctx->pd, ctx->cell_factor, ctx->status);
     }
     {
         Phase p(ctx, SPH_PHASE_KEYS);
-        ctx->launches += launch_keys(L, ctx->n, ctx->st[ctx->cur], ctx->patch_of, ctx->pd, ctx->keys, ctx->vals);
+        ctx->launches += launch_keys(L, ctx->n, s, ctx->patch_of, ctx->pd, ctx->keys, ctx->vals);
     }
     {
         Phase p(ctx, SPH_PHASE_SORT);
@@ -354,7 +379,10 @@ void enqueue_sort(sph_ctx* ctx)
         const int nxt = 1 - ctx->cur;
         ctx->launches += launch_gather(L, ctx->n, ctx->keys, ctx->vals, ctx->st[ctx->cur], ctx->st[nxt],
                                        ctx->perm[ctx->cur], ctx->perm[nxt], ctx->pd, ctx->grid, ctx->rec,
-                                       ctx->f64, ctx->mixed, RowHint{ctx->cnt, ctx->hint_ok, ctx->rowcap});
+                                       ctx->f64, ctx->mixed,
+                                       superset ? RowHint{ctx->cnt_s, ctx->hint_ok_s, ctx->rowcap}
+                                                : RowHint{ctx->cnt, ctx->hint_ok, ctx->rowcap},
+                                       superset ? ctx->hsearch_pre : nullptr, superset ? ctx->skinref.h0 : nullptr);
         ctx->launches += launch_cell_boxes(L, ctx->npatch, ctx->pd, ctx->grid, ctx->rec.r4);
         ctx->cur = nxt;
     }
@@ -372,7 +400,7 @@ void enqueue_lists(sph_ctx* ctx)
     ctx->canon_valid = false;
     {
         Phase p(ctx, SPH_PHASE_NB);
-        ctx->launches += launch_nb_lists(L, a, stencil_k(ctx->cell_factor));
+        ctx->launches += launch_nb_lists(L, a, stencil_k(ctx->cell_factor), 1);
     }
     // the row lengths now belong to the current order: hints for the next sort
     cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
@@ -407,10 +435,55 @@ void enqueue_momentum(sph_ctx* ctx)
         ctx->launches += launch_momentum(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
 }
 
-void enqueue_step(sph_ctx* ctx)
+// the candidate superset of reused lists on the grid of the last sort (its
+// radius scaled by 1 + skin), and the state it was built on
+void enqueue_superset(sph_ctx* ctx)
 {
-    enqueue_sort(ctx);
-    if (!ctx->fused) enqueue_lists(ctx);
+    const Launch L = launch_of(ctx);
+    NbArgs a = nb_args(ctx);
+    a.h = ctx->skinref.h0;       // the search h (no exact decisions in a superset)
+    a.col = ctx->col_s;
+    a.cnt = ctx->cnt_s;
+    a.max_pairs = ctx->max_pairs_s;
+    {
+        Phase p(ctx, SPH_PHASE_NB_RESET);
+        cudaMemsetAsync(ctx->pool_used, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_NB);
+        ctx->launches += launch_nb_lists(L, a, stencil_k(ctx->cell_factor), 0);
+        ctx->launches += launch_skin_snapshot(L, ctx->n, ctx->st[ctx->cur], ctx->skinref);
+    }
+    cudaMemsetAsync(ctx->hint_ok_s, 1, sizeof(int), ctx->stream);
+}
+
+// the exact lists of the current state from the superset: records of the
+// current positions and h on the grid of the last sort, then the filter
+void enqueue_filter(sph_ctx* ctx)
+{
+    const Launch L = launch_of(ctx);
+    {
+        Phase p(ctx, SPH_PHASE_GATHER);
+        ctx->launches += launch_refresh_records(L, ctx->n, ctx->st[ctx->cur], ctx->patch_of, ctx->pd,
+                                                ctx->grid.cellxyz, ctx->rec, ctx->f64, ctx->mixed);
+    }
+    {
+        Phase p(ctx, SPH_PHASE_NB_RESET);
+        cudaMemsetAsync(ctx->pool_used + 1, 0, sizeof(unsigned long long), ctx->stream);
+    }
+    ctx->canon_valid = false;
+    {
+        Phase p(ctx, SPH_PHASE_NB);
+        ctx->launches += launch_nb_filter(L, nb_args(ctx), ctx->col_s, ctx->cnt_s);
+    }
+    cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
+}
+
+bool reuse_lists(const sph_ctx* ctx) { return ctx->skin > 0.0 && !ctx->fused; }
+
+// density, dt, momentum, update (the step after its neighbour phase)
+void enqueue_pair_phases(sph_ctx* ctx)
+{
     enqueue_density(ctx);
     const Launch L = launch_of(ctx);
     {
@@ -427,7 +500,27 @@ void enqueue_step(sph_ctx* ctx)
         const StepArgs a = step_args(ctx);
         ctx->launches += launch_update(L, a);
         ctx->launches += launch_step_finalize(L, a);
+        if (reuse_lists(ctx))
+            ctx->launches += launch_skin_check(L, ctx->n, ctx->st[ctx->cur], ctx->patch_of, ctx->pd, ctx->skinref,
+                                               ctx->skin_red, ctx->skin_flag);
     }
+}
+
+// one step; with reused lists, rebuild = 0 filters the current superset
+// instead of sorting and searching
+void enqueue_step(sph_ctx* ctx, bool rebuild = true)
+{
+    if (reuse_lists(ctx)) {
+        if (rebuild) {
+            enqueue_sort(ctx, true);
+            enqueue_superset(ctx);
+        }
+        enqueue_filter(ctx);
+    } else {
+        enqueue_sort(ctx);
+        if (!ctx->fused) enqueue_lists(ctx);
+    }
+    enqueue_pair_phases(ctx);
 }
 
 sph_status check_status(sph_ctx* ctx, const char* where)
@@ -522,10 +615,11 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
     while ((1 << bits) < np) bits++;
     ctx->radix_passes = (kPatchShift + bits + 7) / 8;
     ctx->patch_off.assign(offsets, offsets + np + 1);
-    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
+    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = ctx->sup_valid = false;
     destroy_graphs(ctx);
     // new particle order: no row-length hints
     CK(cudaMemsetAsync(ctx->hint_ok, 0, sizeof(int), ctx->stream));
+    if (ctx->hint_ok_s) CK(cudaMemsetAsync(ctx->hint_ok_s, 0, sizeof(int), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return after_launches(ctx, "setup_patches");
 }
@@ -601,6 +695,7 @@ void sph_destroy(sph_ctx* ctx)
     for (void* p : ctx->allocs)
         if (p) cudaFree(p);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_skin_flag) cudaFreeHost(ctx->h_skin_flag);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -619,6 +714,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     if (cfg.kernel == SPH_KERNEL_SINC && !(cfg.kernel_n >= 2 && cfg.kernel_n <= 16))
         return fail(nullptr, SPH_EINVAL, "kernel_n must be in [2, 16] for the Sinc kernel");
     if (cfg.grad_h != 0 && cfg.grad_h != 1) return fail(nullptr, SPH_EINVAL, "grad_h must be 0 or 1");
+    if (!(cfg.list_skin >= 0.0 && cfg.list_skin <= 1.0))
+        return fail(nullptr, SPH_EINVAL, "list_skin must be in [0, 1]");
     if (cfg.pair_mode != SPH_PAIRS_LISTS && cfg.pair_mode != SPH_PAIRS_FUSED && cfg.pair_mode != SPH_PAIRS_AUTO)
         return fail(nullptr, SPH_EINVAL, "pair_mode must be SPH_PAIRS_LISTS, SPH_PAIRS_FUSED or SPH_PAIRS_AUTO");
     if (cfg.max_particles < 1 || cfg.max_particles > kMaxParticles)
@@ -671,6 +768,15 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     // second one: 5/2 max_pairs + 24 per particle holds any step whose lists
     // fit in max_pairs after a step whose lists did
     ctx->pool_cap = ctx->max_pairs * 5 / 2 + 24 * cfg.max_particles + 64;
+    ctx->skin = cfg.list_skin;
+    if (ctx->skin > 0.0) {
+        // the superset lists pairs within (1 + skin) times the radius: about
+        // (1 + skin)^3 as many; the exact rows sit at the superset's offsets,
+        // so both pools take the superset's size
+        const double g = 1.0 + ctx->skin;
+        ctx->max_pairs_s = (int64_t)((double)ctx->max_pairs * g * g * g * 1.1) + 64;
+        ctx->pool_cap = ctx->max_pairs_s * 5 / 2 + 24 * cfg.max_particles + 64;
+    }
     ctx->cap_items = (int)(ctx->cap_n / kItemChunk + ctx->cap_patch + 1);
     ctx->cap_cells = 2 * ctx->cap_n + (int64_t)4096 * ctx->cap_patch;
     const size_t N = (size_t)ctx->cap_n;
@@ -713,6 +819,14 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
          dalloc(ctx, ctx->items, (size_t)ctx->cap_items) && dalloc(ctx, ctx->partials, (size_t)ctx->cap_items * 7) &&
          dalloc(ctx, ctx->cons, (size_t)ctx->cap_patch * 7) && dalloc(ctx, ctx->scratch, N) &&
          dalloc(ctx, ctx->status, 1) && dalloc(ctx, ctx->pair_acc, 1) && dalloc(ctx, ctx->hfac, (size_t)kHFacN);
+    if (ctx->skin > 0.0) {
+        ok = ok && dalloc(ctx, ctx->col_s, (size_t)ctx->pool_cap) && dalloc(ctx, ctx->cnt_s, N) &&
+             dalloc(ctx, ctx->hint_ok_s, 1) && dalloc(ctx, ctx->skinref.x0, N) && dalloc(ctx, ctx->skinref.y0, N) &&
+             dalloc(ctx, ctx->skinref.z0, N) && dalloc(ctx, ctx->skinref.h0, N) && dalloc(ctx, ctx->skin_red, 2) &&
+             dalloc(ctx, ctx->hsearch_pre, N) &&
+             dalloc(ctx, ctx->skin_flag, 1);
+        if (ok && cudaMallocHost(&ctx->h_skin_flag, sizeof(int)) != cudaSuccess) ok = false;
+    }
     ctx->grid.patch_of = ctx->patch_of;
     if (ok && cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
@@ -794,10 +908,23 @@ sph_status sph_find_neighbors(sph_ctx* ctx)
 {
     sph_status st = begin_call(ctx);
     if (st != SPH_OK) return st;
+    const bool reuse = reuse_lists(ctx);
+    // with reused lists: the superset of the current order while it still
+    // holds every pair (as a step would take it), else a fresh one
+    const bool rebuild = !reuse || !ctx->sup_valid;
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
-    destroy_graphs(ctx);
-    enqueue_sort(ctx);
-    enqueue_lists(ctx);
+    ctx->sup_valid = ctx->sup_valid && reuse;
+    if (rebuild) destroy_graphs(ctx);
+    if (reuse) {
+        if (rebuild) {
+            enqueue_sort(ctx, true);
+            enqueue_superset(ctx);
+        }
+        enqueue_filter(ctx);
+    } else {
+        enqueue_sort(ctx);
+        enqueue_lists(ctx);
+    }
     st = after_launches(ctx, "sph_find_neighbors");
     if (st != SPH_OK) return st;
     unsigned long long nnz = 0;
@@ -806,6 +933,10 @@ sph_status sph_find_neighbors(sph_ctx* ctx)
     ctx->nnz = (int64_t)nnz;
     if (st != SPH_OK) return st;
     ctx->nb_valid = true;
+    if (reuse) {
+        ctx->sup_valid = true;
+        if (rebuild) ctx->rebuilds++;
+    }
     return SPH_OK;
 }
 
@@ -895,14 +1026,20 @@ sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last)
     if (nsteps < 0) return fail(ctx, SPH_EINVAL, "nsteps < 0");
     if (ctx->n == 0) return SPH_OK;
     const bool graph = ctx->cfg.use_graph && !ctx->prof;
+    const bool reuse = reuse_lists(ctx);
     for (int k = 0; k < nsteps; k++) {
-        if (graph) {
-            const int par = ctx->cur;
-            if (!ctx->gexec[par]) {
+        // with reused lists: sort and search only when the superset no longer
+        // holds every pair (the previous step's check says so)
+        const bool rebuild = !reuse || !ctx->sup_valid;
+        // the first step after new particles runs outside the graphs: a
+        // captured step must not depend on the state having no search yet
+        if (graph && !ctx->fresh) {
+            const int par = ctx->cur, kind = rebuild ? 1 : 0;
+            if (!ctx->gexec[par][kind]) {
                 cudaGraph_t g = nullptr;
                 const int64_t l0 = ctx->launches;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-                enqueue_step(ctx);
+                enqueue_step(ctx, rebuild);
                 cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
                 ctx->cur = par;
                 ctx->launches = l0;
@@ -917,17 +1054,24 @@ sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last)
                     cudaGraphNodeGetType(nd, &ty);
                     if (ty == cudaGraphNodeTypeKernel) nk++;
                 }
-                e = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
+                e = cudaGraphInstantiate(&ctx->gexec[par][kind], g, 0);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
-                ctx->graph_kernels[par] = nk;
+                ctx->graph_kernels[par][kind] = nk;
             }
-            CK(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
-            ctx->launches += ctx->graph_kernels[par];
-            ctx->cur = 1 - par;
+            CK(cudaGraphLaunch(ctx->gexec[par][kind], ctx->stream));
+            ctx->launches += ctx->graph_kernels[par][kind];
+            // a step with a sort moves the state to the other buffer
+            ctx->cur = rebuild ? 1 - par : par;
             ctx->fresh = false;
         } else {
-            enqueue_step(ctx);
+            enqueue_step(ctx, rebuild);
+        }
+        if (reuse) {
+            CK(cudaMemcpyAsync(ctx->h_skin_flag, ctx->skin_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            ctx->sup_valid = *ctx->h_skin_flag != 0;
+            if (rebuild) ctx->rebuilds++;
         }
     }
     st = after_launches(ctx, "sph_step");
@@ -1200,7 +1344,7 @@ sph_status sph_autotune(sph_ctx* ctx)
     ctx->tpp_pair = best_pair;
     ctx->fused = best_fused;
     ctx->prof = prof0;
-    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = false;
+    ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = ctx->sup_valid = false;
     st = after_launches(ctx, "sph_autotune");
     if (st != SPH_OK) return st;
     return check_status(ctx, "sph_autotune");
@@ -1218,6 +1362,13 @@ sph_status sph_get_pair_mode(sph_ctx* ctx, int32_t* mode)
 {
     if (!ctx) return fail(nullptr, SPH_EINVAL, "ctx is NULL");
     if (mode) *mode = ctx->fused ? SPH_PAIRS_FUSED : SPH_PAIRS_LISTS;
+    return SPH_OK;
+}
+
+sph_status sph_get_list_rebuilds(sph_ctx* ctx, int64_t* n)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    if (n) *n = ctx->rebuilds;
     return SPH_OK;
 }
 

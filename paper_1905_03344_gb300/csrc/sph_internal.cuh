@@ -192,10 +192,18 @@ struct RowHint {
     const int* valid;            // nonzero: cnt_prev belongs to the order being gathered from
     uint32_t* rowcap;            // out: hint per new sorted slot, kNoHint if none
 };
+// hsearch (optional, the order gathered from): the h of the search when it
+// is not the particles' h (the candidate superset of reused lists), gathered
+// into hsearch_out and used for the search records and cell maxima
 int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint32_t* svals,
                   const State& src, const State& dst, const uint32_t* perm_src,
                   uint32_t* perm_dst, const PatchDev* pd, const Grid& g, const Recs& r,
-                  const Fp64& f, int mixed, const RowHint& hint);
+                  const Fp64& f, int mixed, const RowHint& hint, const double* hsearch = nullptr,
+                  double* hsearch_out = nullptr);
+// the FP32 records of the current state in the current sorted order, on the
+// grid of the last sort (what the gather writes, with the unscaled h)
+int launch_refresh_records(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of,
+                           const PatchDev* pd, const uint32_t* cellxyz, const Recs& r, const Fp64& f, int mixed);
 // tight boxes of the fine cells (after the gather)
 int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4);
 // temporary words of the device-wide exclusive scan over n values
@@ -220,7 +228,12 @@ struct NbArgs {
     int* status;
 };
 // K: stencil half-extent of every patch (1 for cell_factor >= 1, else 2)
-int launch_nb_lists(const Launch& L, const NbArgs& a, int K);
+// exact = 1: the neighbour lists and n_i; exact = 0: the candidate superset
+// of reused lists (every candidate within the grid's scaled search radius)
+int launch_nb_lists(const Launch& L, const NbArgs& a, int K, int exact);
+// exact lists (a.col, a.cnt, a.nown; rows at a.rowstart) from the superset
+// rows col_s / cnt_s at the same offsets, on the current records and state
+int launch_nb_filter(const Launch& L, const NbArgs& a, const uint32_t* col_s, const uint32_t* cnt_s);
 int launch_canonical_rows(const Launch& L, int64_t n, const unsigned long long* rowstart,
                           const uint32_t* cnt, const uint64_t* off, const uint32_t* col, uint32_t* out);
 // exclusive scan of n u32 values into u64 out[0..n], out[n] = total
@@ -273,6 +286,20 @@ struct StepArgs {
 int launch_hc_min(const Launch& L, const StepArgs& a);
 int launch_dt(const Launch& L, const StepArgs& a);
 int launch_update(const Launch& L, const StepArgs& a);
+// reused candidate supersets: the state the superset was built on (sorted
+// order), and the check that it still holds every neighbour pair
+struct SkinRef {
+    double *x0, *y0, *z0;  // positions the superset was built on
+    double* h0;            // its search h (the superset lists r < 2 max(h0_i, h0_j))
+};
+int launch_skin_snapshot(const Launch& L, int64_t n, const State& s, const SkinRef& ref);
+// the superset's search h per particle (current order): h (1 + skin + 3 (f - 1)+),
+// f the h-adaptation factor of the last step (from n_i; 1 when nown is NULL)
+int launch_skin_radius(const Launch& L, int64_t n, const State& s, const uint32_t* nown, const double* hfac,
+                       double n_target, double skin, double* hsearch);
+// flag (device) = 1 while max |x - x0| <= min (h0 - h), h0 = the superset's search h
+int launch_skin_check(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of, const PatchDev* pd,
+                      const SkinRef& ref, unsigned long long* red, int* flag);
 int launch_conserved_items(const Launch& L, const StepArgs& a);
 int launch_conserved_finalize(const Launch& L, const StepArgs& a);
 int launch_step_finalize(const Launch& L, const StepArgs& a);

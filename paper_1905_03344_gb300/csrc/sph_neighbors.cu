@@ -15,17 +15,18 @@
 // depends on scheduling, and every consumer reads a row through its start
 // and length, so all results are bitwise reproducible.  The canonical CSR
 // with prefix offsets is built from the pool on demand (sph_get_neighbors).
+#include "sph_pairmath.cuh"
 #include "sph_walk.cuh"
 
 namespace sphg {
 
 // counting walk (col = nullptr) and repair walk (straight to the pool): one
 // out-of-line copy serves both
-template <int K>
-__device__ __noinline__ RowSink<kWalkFlat> walk_all_flat(const NbArgs& a, const PatchDev* P, int64_t i, bool big,
-                                                      RowSink<kWalkFlat> row)
+template <int K, bool EXACT>
+__device__ __noinline__ RowSink<kWalkFlat, EXACT> walk_all_flat(const NbArgs& a, const PatchDev* P, int64_t i,
+                                                             bool big, RowSink<kWalkFlat, EXACT> row)
 {
-    walk_all<RowSink<kWalkFlat>, K>(a, P, i, big, row);
+    walk_all<RowSink<kWalkFlat, EXACT>, K>(a, P, i, big, row);
     return row;
 }
 
@@ -38,8 +39,10 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
     return v;
 }
 
-// K: stencil half-extent, the same for every patch (it follows cell_factor)
-template <int K>
+// K: stencil half-extent, the same for every patch (it follows cell_factor);
+// EXACT = false: the candidate superset (every candidate within the scaled
+// search radius in FP32, no n_i)
+template <int K, bool EXACT>
 __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArgs a)
 {
     extern __shared__ __align__(16) uint32_t nb_ring[];
@@ -59,7 +62,8 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         if (act) {
             const uint32_t hint = a.rowcap[i];
             if (hint == kNoHint) {
-                const RowSink<kWalkFlat> rc = walk_all_flat<K>(a, P, i, big, RowSink<kWalkFlat>{nullptr, nullptr, 0u, 0u, 0u});
+                const RowSink<kWalkFlat, EXACT> rc =
+                    walk_all_flat<K, EXACT>(a, P, i, big, RowSink<kWalkFlat, EXACT>{nullptr, nullptr, 0u, 0u, 0u});
                 res = round8(rc.cnt);
             } else {
                 const uint32_t c = min(hint, (uint32_t)a.n);
@@ -74,9 +78,9 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         const bool ok = base + tot <= pool_cap;
         if (!ok && lane == 0) atomicOr(a.status, kStOverflow);
         unsigned long long r0 = base + (inc - res);
-        RowSink<kWalkRing> row = {a.col + r0, ring, ok ? res : 0u, 0u, 0u};
+        RowSink<kWalkRing, EXACT> row = {a.col + r0, ring, ok ? res : 0u, 0u, 0u};
         if (act) {
-            walk_all<RowSink<kWalkRing>, K>(a, P, i, big, row);
+            walk_all<RowSink<kWalkRing, EXACT>, K>(a, P, i, big, row);
             row.finish();
         }
         if (act && ok && row.cnt > res) {
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
             const uint32_t need = round8(row.cnt);
             r0 = atomicAdd(&a.pool_used[0], (unsigned long long)need);
             if (r0 + need <= pool_cap) {
-                walk_all_flat<K>(a, P, i, big, RowSink<kWalkFlat>{a.col + r0, nullptr, need, 0u, 0u});
+                walk_all_flat<K, EXACT>(a, P, i, big, RowSink<kWalkFlat, EXACT>{a.col + r0, nullptr, need, 0u, 0u});
             } else {
                 atomicOr(a.status, kStOverflow);
             }
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         if (act) {
             a.rowstart[i] = r0;
             a.cnt[i] = row.cnt;
-            a.nown[i] = row.own;
+            if (EXACT) a.nown[i] = row.own;
         }
         const uint32_t listed = __shfl_sync(0xffffffffu, warp_incl_scan(act ? row.cnt : 0u, lane), 31);
         if (lane == 0) {
@@ -102,13 +106,13 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
     }
 }
 
-template <int K>
+template <int K, bool EXACT>
 void launch_nb_thread(const Launch& L, const NbArgs& a)
 {
     const size_t smem = sizeof(uint32_t) * 32 * kRing * kNbtWarps;
     static int per_sm = 0;
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_thread<K>, 32 * kNbtWarps, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_thread<K, EXACT>, 32 * kNbtWarps, smem);
         if (per_sm < 1) per_sm = 1;
         // shared memory only for the rings of the resident CTAs: the rest is L1
         int smem_max = 0, dev = 0;
@@ -118,18 +122,121 @@ void launch_nb_thread(const Launch& L, const NbArgs& a)
             const size_t need = (size_t)per_sm * (smem + 1024);
             int pct = (int)((need * 100 + (size_t)smem_max - 1) / (size_t)smem_max);
             pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
-            cudaFuncSetAttribute(k_nb_thread<K>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(k_nb_thread<K, EXACT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
     }
-    k_nb_thread<K><<<L.sms * per_sm, 32 * kNbtWarps, smem, L.stream>>>(a);
+    k_nb_thread<K, EXACT><<<L.sms * per_sm, 32 * kNbtWarps, smem, L.stream>>>(a);
 }
 
-int launch_nb_lists(const Launch& L, const NbArgs& a, int K)
+int launch_nb_lists(const Launch& L, const NbArgs& a, int K, int exact)
 {
     if (a.n <= 0 || a.nunits <= 0) return 0;
-    if (K == 1) launch_nb_thread<1>(L, a);
-    else if (K == 2) launch_nb_thread<2>(L, a);
-    else launch_nb_thread<3>(L, a);
+    if (exact) {
+        if (K == 1) launch_nb_thread<1, true>(L, a);
+        else if (K == 2) launch_nb_thread<2, true>(L, a);
+        else launch_nb_thread<3, true>(L, a);
+    } else {
+        if (K == 1) launch_nb_thread<1, false>(L, a);
+        else if (K == 2) launch_nb_thread<2, false>(L, a);
+        else launch_nb_thread<3, false>(L, a);
+    }
+    return 1;
+}
+
+// ---- exact lists from a reused candidate superset -------------------------
+// Row i of the superset (col_s from rowstart[i], cnt_s[i] words, built on an
+// earlier state with the search radius scaled by 1 + skin) is decided again
+// on the current state: the FP32 test on the records refreshed for the
+// current positions and h, and the exact FP64 predicate inside the guard
+// band, as in the search.  The accepted words keep their order and go to
+// the exact pool at the same offset.  A group of TPP lanes per row: each
+// lane decides one word per round; the group ballots and writes the accepted
+// words contiguously.  Groups of a warp run their rounds together (a shorter
+// row idles through the longer one's last rounds), so TPP = 32: one row per
+// warp in lockstep.
+template <int TPP>
+__global__ void __launch_bounds__(256) k_nb_filter(NbArgs a, const uint32_t* col_s, const uint32_t* cnt_s)
+{
+    __shared__ float4 tab[kStencilCells];
+    fill_stencil_table(tab);
+    if (*a.status & kStBad) return;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (TPP - 1);
+    const unsigned gmask = TPP == 32 ? 0xffffffffu : (((1u << TPP) - 1u) << (lane & ~(TPP - 1)));
+    const unsigned below = (1u << lane) - 1u;    // lanes before this one
+    const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
+    unsigned long long listed = 0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+        const PatchDev* P = a.pd + a.g.patch_of[i];
+        const float s_f = P->s_f, sz_f = P->sz_f, lz_f = P->lz_f;
+        const int zmode = P->zmode, Dcode = zmode ? max(2, P->ncz) : 2;
+        const float4 ri = a.r4[i];
+        const uint32_t ci = a.g.cellxyz[i];
+        const float Ti = ri.w;
+        const float sh = s_f / (float)a.h[i];
+        const unsigned long long rs = a.rowstart[i];
+        const uint32_t len = cnt_s[i];
+        uint32_t out = 0, own = 0;
+        for (uint32_t k0 = 0; k0 < len; k0 += TPP) {
+            const uint32_t k = k0 + (uint32_t)gl;
+            bool in = false, io = false;
+            uint32_t w = 0;
+            if (k < len) {
+                w = col_s[rs + k];
+                const uint32_t j = w & kColMask;
+                const float4 q = a.r4[j];
+                const uint32_t code = w >> kColBits;
+                float dx, dy, dz;
+                int D;
+                if (code != kFarCode) {
+                    const float4 e = tab[code];
+                    if (zmode) rel_dx<1>(e, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+                    else rel_dx<0>(e, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+                    D = Dcode;
+                } else {
+                    const uint32_t cj = a.g.cellxyz[j];
+                    rel_dx_far(ci, cj, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+                    const int ax = abs((int)(cj & 255u) - (int)(ci & 255u));
+                    const int ay = abs((int)((cj >> 8) & 255u) - (int)((ci >> 8) & 255u));
+                    const int az = abs((int)(cj >> 16) - (int)(ci >> 16));
+                    D = max(ax, max(ay, az));
+                }
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float T = fmaxf(Ti, q.w);
+                const float tol = guard_tol(sh, D);
+                const float fhi = 1.0f + tol;
+                if (r2 <= T * fhi) {
+                    const int d = pair_decision(a, P, i, j, r2, Ti, T, 1.0f - tol, fhi);
+                    in = d & 1;
+                    io = (d >> 1) & 1;
+                }
+            }
+            const unsigned bin = __ballot_sync(gmask, in) & gmask;
+            const unsigned bio = __ballot_sync(gmask, io) & gmask;
+            if (in) a.col[rs + out + (uint32_t)__popc(bin & below)] = w;
+            out += (uint32_t)__popc(bin);
+            own += (uint32_t)__popc(bio);
+        }
+        if (gl == 0) {
+            a.cnt[i] = out;
+            a.nown[i] = own;
+            listed += out;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) listed += __shfl_xor_sync(0xffffffffu, listed, o);
+    if (lane == 0 && listed) {
+        const unsigned long long before = atomicAdd(&a.pool_used[1], listed);
+        if (before + listed > (unsigned long long)a.max_pairs) atomicOr(a.status, kStOverflow);
+    }
+}
+
+int launch_nb_filter(const Launch& L, const NbArgs& a, const uint32_t* col_s, const uint32_t* cnt_s)
+{
+    if (a.n <= 0) return 0;
+    constexpr int TPP = 32;
+    int64_t blocks = (a.n * TPP + 255) / 256;
+    if (blocks > (int64_t)L.sms * 8) blocks = (int64_t)L.sms * 8;
+    k_nb_filter<TPP><<<(unsigned)blocks, 256, 0, L.stream>>>(a, col_s, cnt_s);
     return 1;
 }
 

@@ -557,10 +557,48 @@ int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, ui
 // the time-centred velocity v_{n-1/2} + a_{n-1} dt_{n-1}/2 used by the
 // viscosity and the energy equation.
 // ---------------------------------------------------------------------------
+// the FP32 records of sorted slot k in cell (cx, cy, cz) of patch P: offsets
+// from the cell origin, 4 hq^2 (hq: the h of the search), and for
+// the pair sums the mass, the time-centred velocity v + a_{n-1} dt_{n-1}/2
+// and 1/(2h) (mixed), or the same in FP64.  The z offset is taken from the
+// image of z nearest the cell's centre: a particle that has left its cell
+// since the sort (reused lists) may have crossed the periodic z boundary, and
+// the pair separation, which wraps at most once, needs every offset within
+// about a cell of its cell.  A particle inside its cell is its own nearest
+// image, so this changes nothing right after a sort.
+__device__ __forceinline__ void write_records(int64_t k, const PatchDev* P, uint32_t cx, uint32_t cy, uint32_t cz,
+                                              double x, double y, double z, double vx, double vy, double vz,
+                                              double m, double h, double u, double axp, double ayp, double azp,
+                                              float hq, Recs& r, Fp64& f, int mixed)
+{
+    const float ox = (float)(x - (P->xmin + (double)cx * P->s));
+    const float oy = (float)(y - (P->ymin + (double)cy * P->s));
+    double ozd = z - (-0.5 * P->lz + (double)cz * P->sz);
+    const double oc = ozd - 0.5 * P->sz;
+    if (oc > 0.5 * P->lz) ozd -= P->lz;
+    else if (oc < -0.5 * P->lz) ozd += P->lz;
+    const float oz = (float)ozd;
+    const float hf = (float)h;
+    r.r4[k] = make_float4(ox, oy, oz, 4.0f * hq * hq);
+    const double half = P->step > 0 ? 0.5 * P->dt_prev : 0.0;
+    const double vhx = vx + axp * half, vhy = vy + ayp * half, vhz = vz + azp * half;
+    if (mixed) {
+        r.r5[k] = make_float4(ox, oy, oz, (float)m);
+        r.rv[k] = make_float4((float)vhx, (float)vhy, (float)vhz, 0.5f / hf);
+        r.uf[k] = (float)u;
+    } else {
+        f.vhx[k] = vhx;
+        f.vhy[k] = vhy;
+        f.vhz[k] = vhz;
+        f.invh[k] = 1.0 / h;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys, const uint32_t* svals,
                                                 State src, State dst, const uint32_t* perm_src,
                                                 uint32_t* perm_dst, const PatchDev* pd, Grid g,
-                                                Recs r, Fp64 f, int mixed, RowHint hint)
+                                                Recs r, Fp64 f, int mixed, RowHint hint,
+                                                const double* hsearch, double* hsearch_out)
 {
     const bool have_hint = *hint.valid != 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -585,23 +623,10 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
         const bool big = (key >> kClassShift) & 1u;
         const uint32_t cx = compact1by2(mort), cy = compact1by2(mort >> 1), cz = compact1by2(mort >> 2);
         g.cellxyz[k] = cx | (cy << 8) | (cz << 16);
-        const float ox = (float)(x - (P->xmin + (double)cx * P->s));
-        const float oy = (float)(y - (P->ymin + (double)cy * P->s));
-        const float oz = (float)(z - (-0.5 * P->lz + (double)cz * P->sz));
-        const float hf = (float)h;
-        r.r4[k] = make_float4(ox, oy, oz, 4.0f * hf * hf);
-        const double half = P->step > 0 ? 0.5 * P->dt_prev : 0.0;
-        const double vhx = vx + axp * half, vhy = vy + ayp * half, vhz = vz + azp * half;
-        if (mixed) {
-            r.r5[k] = make_float4(ox, oy, oz, (float)m);
-            r.rv[k] = make_float4((float)vhx, (float)vhy, (float)vhz, 0.5f / hf);
-            r.uf[k] = (float)dst.u[k];
-        } else {
-            f.vhx[k] = vhx;
-            f.vhy[k] = vhy;
-            f.vhz[k] = vhz;
-            f.invh[k] = 1.0 / h;
-        }
+        // h of the search
+        const float hf = (float)(hsearch ? hsearch[si] : h);
+        if (hsearch_out) hsearch_out[k] = hsearch[si];
+        write_records(k, P, cx, cy, cz, x, y, z, vx, vy, vz, m, h, dst.u[k], axp, ayp, azp, hf, r, f, mixed);
         if (!big) {
             // fine cell of small particles: bounded by a change of key
             const int64_t lin = P->cell_base + ((int64_t)cz * P->ncy + cy) * P->ncx + cx;
@@ -625,11 +650,37 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t* skeys
 int launch_gather(const Launch& L, int64_t n, const uint32_t* skeys, const uint32_t* svals,
                   const State& src, const State& dst, const uint32_t* perm_src, uint32_t* perm_dst,
                   const PatchDev* pd, const Grid& g, const Recs& r, const Fp64& f, int mixed,
-                  const RowHint& hint)
+                  const RowHint& hint, const double* hsearch, double* hsearch_out)
 {
     if (n <= 0) return 0;
     k_gather<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, skeys, svals, src, dst, perm_src,
-                                                                 perm_dst, pd, g, r, f, mixed, hint);
+                                                                 perm_dst, pd, g, r, f, mixed, hint, hsearch,
+                                                                 hsearch_out);
+    return 1;
+}
+
+// records of the current state without a sort (between rebuilds of a reused
+// candidate superset): the grid and cells of the last sort, the current
+// positions, h and time state
+__global__ void __launch_bounds__(256) k_refresh_records(int64_t n, State s, const uint16_t* patch_of,
+                                                         const PatchDev* pd, const uint32_t* cellxyz, Recs r,
+                                                         Fp64 f, int mixed)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const PatchDev* P = pd + patch_of[k];
+        const uint32_t c = cellxyz[k];
+        const double h = s.h[k];
+        write_records(k, P, c & 255u, (c >> 8) & 255u, c >> 16, s.x[k], s.y[k], s.z[k], s.vx[k], s.vy[k], s.vz[k],
+                      s.m[k], h, s.u[k], s.axp[k], s.ayp[k], s.azp[k], (float)h, r, f, mixed);
+    }
+}
+
+int launch_refresh_records(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of,
+                           const PatchDev* pd, const uint32_t* cellxyz, const Recs& r, const Fp64& f, int mixed)
+{
+    if (n <= 0) return 0;
+    k_refresh_records<<<blocks_for(n, 256, L.sms, 16), 256, 0, L.stream>>>(n, s, patch_of, pd, cellxyz, r, f,
+                                                                          mixed);
     return 1;
 }
 

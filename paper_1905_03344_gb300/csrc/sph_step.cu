@@ -81,12 +81,20 @@ __global__ void __launch_bounds__(256) k_hc_min(StepArgs a)
     }
 }
 
+// every step starts its minima afresh (a step that reuses its lists runs no
+// sort, whose reset would otherwise clear them)
+__global__ void k_hc_reset(PatchRed* red, int npatch)
+{
+    for (int p = threadIdx.x; p < npatch; p += blockDim.x) red[p].hcmin = ~0ull;
+}
+
 int launch_hc_min(const Launch& L, const StepArgs& a)
 {
     if (a.nitems <= 0) return 0;
+    k_hc_reset<<<1, 256, 0, L.stream>>>(a.red, a.npatch);
     const int grid = a.nitems < L.sms * 8 ? a.nitems : L.sms * 8;
     k_hc_min<<<grid, 256, 0, L.stream>>>(a);
-    return 1;
+    return 2;
 }
 
 // ---- Courant time-step per patch ------------------------------------------
@@ -313,6 +321,110 @@ int launch_validate(const Launch& L, int64_t n, const State& s, int* status)
     if (n <= 0) return 0;
     k_validate<<<grid_n(L, n), 256, 0, L.stream>>>(n, s, status);
     return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Reused candidate supersets.  The superset built on state 0 with the search
+// h g_k of every particle (g_k >= h_k0) lists every pair with
+// r0 < 2 max(g_i, g_j).  It still holds every neighbour pair of the current
+// state while D = max_k |x_k - x_k0| <= min_k (g_k - h_k): for a pair with
+// r < 2 max(h_i, h_j), say h_i >= h_j, r0 <= r + 2 D < 2 (h_i + D) <= 2 g_i
+// (distances and displacements with the minimum image along z).
+// g_k = h_k (1 + skin + 3 (f_k - 1)+), f_k the factor the last step's h
+// adaptation applied: particles whose h is growing (a free surface, where
+// they have too few neighbours) get the room for a few more steps of it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_skin_radius(int64_t n, State s, const uint32_t* nown, const double* hfac,
+                                                     double n_target, double skin, double* hsearch)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double f = 1.0;
+        if (nown) {
+            const uint32_t ni = nown[k];
+            if (ni == 0) f = 2.0;
+            else if (ni < (uint32_t)kHFacN) f = hfac[ni];
+            else f = 0.5 * (1.0 + cbrt(n_target / (double)ni));
+        }
+        const double g = 1.0 + skin + 3.0 * fmax(f - 1.0, 0.0);
+        hsearch[k] = s.h[k] * fmin(g, 4.0);
+    }
+}
+
+int launch_skin_radius(const Launch& L, int64_t n, const State& s, const uint32_t* nown, const double* hfac,
+                       double n_target, double skin, double* hsearch)
+{
+    if (n <= 0) return 0;
+    k_skin_radius<<<grid_n(L, n), 256, 0, L.stream>>>(n, s, nown, hfac, n_target, skin, hsearch);
+    return 1;
+}
+
+// positions of the build (the search h is already in ref.h0)
+__global__ void __launch_bounds__(256) k_skin_snapshot(int64_t n, State s, double* x0, double* y0, double* z0)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        x0[k] = s.x[k];
+        y0[k] = s.y[k];
+        z0[k] = s.z[k];
+    }
+}
+
+int launch_skin_snapshot(const Launch& L, int64_t n, const State& s, const SkinRef& ref)
+{
+    if (n <= 0) return 0;
+    k_skin_snapshot<<<grid_n(L, n), 256, 0, L.stream>>>(n, s, ref.x0, ref.y0, ref.z0);
+    return 1;
+}
+
+// red[0]: largest displacement, red[1]: smallest slack (ordered-integer
+// encoded); both reset by k_skin_reset
+__global__ void k_skin_reset(unsigned long long* red)
+{
+    red[0] = ord_f64(0.0);
+    red[1] = ord_f64(1e300);
+}
+
+__global__ void __launch_bounds__(256) k_skin_check(int64_t n, State s, const uint16_t* patch_of, const PatchDev* pd,
+                                                    SkinRef ref, unsigned long long* red)
+{
+    double dmax = 0.0, smin = 1e300;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double lz = pd[patch_of[k]].lz;
+        const double dx = s.x[k] - ref.x0[k], dy = s.y[k] - ref.y0[k];
+        double dz = s.z[k] - ref.z0[k];
+        if (dz > 0.5 * lz) dz -= lz;
+        else if (dz < -0.5 * lz) dz += lz;
+        dmax = fmax(dmax, sqrt(dx * dx + dy * dy + dz * dz));
+        smin = fmin(smin, ref.h0[k] - s.h[k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&red[0], ord_f64(dmax));
+        atomicMin(&red[1], ord_f64(smin));
+    }
+}
+
+// flag = 1 while the superset holds (with a relative margin of 1e-9 against
+// the rounding of the two reductions)
+__global__ void k_skin_decide(const unsigned long long* red, int* flag)
+{
+    const double dmax = unord_f64(red[0]), smin = unord_f64(red[1]);
+    *flag = (smin > 0.0 && dmax * (1.0 + 1e-9) <= smin) ? 1 : 0;
+}
+
+int launch_skin_check(const Launch& L, int64_t n, const State& s, const uint16_t* patch_of, const PatchDev* pd,
+                      const SkinRef& ref, unsigned long long* red, int* flag)
+{
+    k_skin_reset<<<1, 1, 0, L.stream>>>(red);
+    int k = 1;
+    if (n > 0) {
+        k_skin_check<<<grid_n(L, n), 256, 0, L.stream>>>(n, s, patch_of, pd, ref, red);
+        k++;
+    }
+    k_skin_decide<<<1, 1, 0, L.stream>>>(red, flag);
+    return k + 1;
 }
 
 }  // namespace sphg

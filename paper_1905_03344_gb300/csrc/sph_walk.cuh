@@ -99,8 +99,9 @@ __device__ __forceinline__ int pair_decision(const NbArgs& a, const PatchDev* P,
 
 __device__ __forceinline__ uint32_t round8(uint32_t v) { return (v + 7u) & ~7u; }
 
-// the row being built by one lane
-template <int MODE>
+// the row being built by one lane; EXACT = false: every candidate that passed
+// the coarse FP32 test (the candidate superset of reused lists), no n_i
+template <int MODE, bool EXACT = true>
 struct RowSink {
     uint32_t* col;      // the row's first pool entry; flat mode: nullptr = count only
     uint32_t* ring;     // this lane's ring (ring mode): slot k at ring[32 k]
@@ -138,6 +139,10 @@ struct RowSink {
     __device__ __forceinline__ void decide(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t j, float r2,
                                            float Ti, float T, float flo, float fhi, uint32_t w)
     {
+        if (!EXACT) {
+            put(w);
+            return;
+        }
         const int d = pair_decision(a, P, i, j, r2, Ti, T, flo, fhi);
         own += (uint32_t)(d >> 1);
         if (d & 1) put(w);

@@ -122,7 +122,8 @@ def test_bad_inputs(B):
 @pytest.mark.parametrize("kw", [dict(cell_factor=0.3), dict(threads_per_particle=3),
                                 dict(max_particles=0), dict(gamma=1.0), dict(max_patches=300),
                                 dict(kernel=2), dict(kernel=1, kernel_n=1), dict(kernel=1, kernel_n=17),
-                                dict(grad_h=2), dict(grad_h=-1), dict(pair_mode=3), dict(pair_mode=-1)])
+                                dict(grad_h=2), dict(grad_h=-1), dict(pair_mode=3), dict(pair_mode=-1),
+                                dict(list_skin=-0.1), dict(list_skin=1.5)])
 def test_bad_config(B, kw):
     mp = kw.pop("max_particles", 8)
     with pytest.raises(B.SphError) as e:

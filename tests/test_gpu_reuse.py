@@ -1,0 +1,188 @@
+"""Reused candidate supersets (list_skin > 0): the search runs only every few
+steps, with its radius scaled by 1 + skin, and each step takes its exact lists
+from that superset.
+
+Every step's lists must still be the exact sets: the counts |N(i)| and n_i
+each step reports are checked bit for bit against the oracle's neighbour
+search on the state that step started from, including steps that only
+filtered the superset.  The density of each step is checked against the
+oracle's on the same state, and whole trajectories against the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1905_03344_gb300 import inputs
+from gpu_common import lists_to_original, normwise
+from test_gpu_parity import _compare_state, cap_pairs, h_tail
+
+pytestmark = pytest.mark.gpu
+
+STEP_CASES = {
+    "patch20": lambda: inputs.square_patch(20),
+    "irregular": lambda: inputs.irregular_patch(14, seed_pos=6, seed_mass=7),
+    # a moving cloud that stays physical over the steps (u > 0 throughout in
+    # the oracle; faster clouds reach negative u and a NaN sound speed)
+    "cloud_v": lambda: inputs.random_cloud(2500, seed=31, h_lo=0.08, h_hi=0.1, vscale=1.0),
+    "htail": lambda: h_tail(4000, 45, 0.07, [(0.01, 0.15, 0.2)]),
+    "zflow": lambda: zflow(),
+}
+
+
+def zflow():
+    """A cloud streaming along the periodic z axis in both directions, so that
+    particles cross z = +-1/2 between rebuilds."""
+    f = inputs.random_cloud(2500, seed=33, h_lo=0.08, h_hi=0.1, vscale=0.2)
+    rng = np.random.default_rng(34)
+    f["vz"] = f["vz"] + np.where(rng.random(2500) < 0.5, 4.0, -4.0)
+    return f
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1905_03344_gb300 import binding, build
+    build.build()
+    binding.lib()
+    return binding
+
+
+@pytest.mark.parametrize("case", sorted(STEP_CASES))
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+@pytest.mark.parametrize("skin", [0.05, 0.25])
+def test_every_step_exact(B, orc, case, precision, tol, skin, report):
+    f = STEP_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    n = len(f["x"])
+    sim = B.SPH(n, precision=precision, lz=lz, list_skin=skin, max_pairs=cap_pairs(n))
+    sim.set_particles(f)
+    worst = 0.0
+    nsteps = 8
+    for step in range(nsteps):
+        s = {k: sim.field(k) for k in ("x", "y", "z", "h", "m", "u")}
+        nb = orc.neighbors(s["x"], s["y"], s["z"], s["h"], lz)
+        # the lists this step will use (from the superset while it holds)
+        sim.find_neighbors()
+        off, col, perm = sim.neighbors()
+        o, c = lists_to_original(off, col, perm, n)
+        assert np.array_equal(o, nb.off) and np.array_equal(c, nb.col), (case, step)
+        sim.step(1)
+        assert np.array_equal(sim.field("nnb").astype(np.int64), np.diff(nb.off)), (case, step)
+        assert np.array_equal(sim.field("nown").astype(np.int64), nb.nown.astype(np.int64)), (case, step)
+        rho = orc.density(s["x"], s["y"], s["z"], s["m"], s["h"], nb, lz)
+        e = normwise(sim.field("rho"), rho)
+        worst = max(worst, e)
+        assert e < tol, (case, step, e)
+    r = sim.list_rebuilds()
+    sim.close()
+    report["reuse/%s/%s/skin%.2f" % (case, precision, skin)] = dict(rho=worst, rebuilds=r, steps=nsteps)
+    assert 1 <= r <= nsteps
+    if skin >= 0.25 and case in ("patch20", "irregular"):
+        assert r < nsteps, "a skin of 0.25 should carry the superset over some steps"
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+def test_reuse_trajectory(B, orc, precision, tol, report):
+    f = inputs.square_patch(20)
+    n = len(f["x"])
+    sim = B.SPH(n, precision=precision, list_skin=0.15)
+    sim.set_particles(f)
+    ref = orc.Sim(f)
+    hist = []
+    for step in range(12):
+        dt = sim.step(1)
+        ref.step(1)
+        assert abs(dt - ref.dt) <= tol * ref.dt, (step, dt, ref.dt)
+        g = {k: sim.field(k) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "nown", "rho",
+                                       "ax", "ay", "az")}
+        assert np.array_equal(g["nown"], ref["nown"]), step
+        hist.append(_compare_state(g, ref, tol, "reuse step %d" % step))
+    report["reuse_steps12/%s" % precision] = dict(errors=hist, rebuilds=sim.list_rebuilds())
+    assert sim.list_rebuilds() < 12
+    sim.close()
+
+
+@pytest.mark.parametrize("case", ["patch20", "htail", "cloud_v"])
+def test_find_neighbors_from_superset(B, orc, case):
+    """sph_find_neighbors with a skin builds the superset and filters it at
+    once: the lists are the oracle's sets."""
+    f = STEP_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    n = len(f["x"])
+    ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"], lz)
+    sim = B.SPH(n, lz=lz, list_skin=0.2, max_pairs=cap_pairs(n))
+    sim.set_particles(f)
+    sim.find_neighbors()
+    off, col, perm = sim.neighbors()
+    o, c = lists_to_original(off, col, perm, n)
+    assert np.array_equal(o, ref.off) and np.array_equal(c, ref.col)
+    assert np.array_equal(sim.field("nown").astype(np.int64), ref.nown.astype(np.int64))
+    assert sim.list_rebuilds() == 1
+    sim.close()
+
+
+def test_reuse_graph_replay_same_bits(B):
+    f = inputs.irregular_patch(14, seed_pos=6, seed_mass=7)
+    n = len(f["x"])
+    out, rb = [], []
+    for graph in (0, 1):
+        sim = B.SPH(n, use_graph=graph, list_skin=0.2)
+        sim.set_particles(f)
+        sim.step(9)
+        out.append({k: sim.field(k) for k in ("x", "vx", "u", "h", "rho", "ax", "nown")})
+        rb.append(sim.list_rebuilds())
+        sim.close()
+    assert rb[0] == rb[1] and rb[0] < 9
+    for k in out[0]:
+        assert np.array_equal(out[0][k].view(np.uint64), out[1][k].view(np.uint64)), k
+
+
+def test_reuse_batched_patches(B, orc):
+    f, offsets, edges, omegas = inputs.batch_patches(5, seed=4)
+    n = len(f["x"])
+    sim = B.SPH(n, max_patches=5, list_skin=0.2)
+    sim.set_particles(f)
+    sim.set_patches(offsets)
+    for step in range(4):
+        s = {k: sim.field(k) for k in ("x", "y", "z", "h")}
+        sim.step(1)
+        nown = sim.field("nown").astype(np.int64)
+        for p in range(5):
+            a, b = int(offsets[p]), int(offsets[p + 1])
+            nb = orc.neighbors(s["x"][a:b], s["y"][a:b], s["z"][a:b], s["h"][a:b])
+            assert np.array_equal(nown[a:b], nb.nown.astype(np.int64)), (step, p)
+    sim.close()
+
+
+def test_reuse_checkpoint_rebuilds(B):
+    """A restored state rebuilds its superset at its first step; in FP64 the
+    continuation then agrees with the uninterrupted run to rounding."""
+    f = inputs.square_patch(16)
+    n = len(f["x"])
+    a = B.SPH(n, precision="fp64", list_skin=0.2)
+    a.set_particles(f)
+    a.step(3)
+    blob = a.get_state()
+    a.step(4)
+    b = B.SPH(n, precision="fp64", list_skin=0.2)
+    b.set_state(blob)
+    b.step(4)
+    assert b.list_rebuilds() >= 1
+    for k in ("x", "y", "z", "u", "h"):
+        assert normwise(b.field(k), a.field(k)) < 1e-13, k
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reuse_empty_and_single(B, precision):
+    sim = B.SPH(4, precision=precision, list_skin=0.1)
+    z = {k: np.zeros(0) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "h", "u")}
+    sim.set_particles(z)
+    sim.step(2)
+    one = {k: np.zeros(1) for k in ("x", "y", "z", "vx", "vy", "vz")}
+    one.update(m=np.full(1, 0.5), h=np.full(1, 0.1), u=np.ones(1), vx=np.ones(1))
+    sim.set_particles(one)
+    sim.step(3)
+    assert sim.field("nnb")[0] == 0
+    sim.close()
