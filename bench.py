@@ -55,13 +55,14 @@ FLOPS_PER_PAIR_MOMENTUM_FP64 = 56
 # (4 B) read once.
 NB_BYTES_PER_ENTRY = 4
 NB_BYTES_PER_PARTICLE = 48
-# DRAM bytes (read + write) per list entry of one launch, from the ncu launch
-# list of the 200^3 patch (dram__bytes_read.sum + dram__bytes_write.sum of a
-# launch divided by its list entries; profiles/launches_square_patch_200cubed.md),
-# scaled to the benchmark's launch by its entries.  None once the kernel has
-# changed since.
-NB_DRAM_BYTES_PER_ENTRY = 5.67
-MOMENTUM_DRAM_BYTES_PER_ENTRY = 5.97
+# DRAM bytes (read + write) per list entry of one launch, from the ncu
+# capture of the same kernels on the 100^3 patch (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the launch's 1.024e8 list entries;
+# profiles/k_nb_thread_square_patch_100cubed.md and
+# profiles/k_momentum_mixed_square_patch_100cubed.md), scaled to the
+# benchmark's launch by its entries.  None once the kernel has changed since.
+NB_DRAM_BYTES_PER_ENTRY = 5.87
+MOMENTUM_DRAM_BYTES_PER_ENTRY = 6.59
 
 WORKLOADS = {
     "c1": ("square patch 20^3 (8,000 particles), omega=5", 20),
