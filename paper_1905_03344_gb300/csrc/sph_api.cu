@@ -44,6 +44,13 @@ __global__ void k_iota(int64_t n, uint32_t* p)
         p[i] = (uint32_t)i;
 }
 
+// dst[perm[k]] = src[k]: a sorted-order array back to the caller's order
+__global__ void k_scatter_u32(int64_t n, const uint32_t* src, const uint32_t* perm, uint32_t* dst)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[perm[k]] = src[k];
+}
+
 __global__ void k_accum_pairs(const unsigned long long* total, unsigned long long* acc, const int* status)
 {
     if (!(*status & kStBad)) *acc += *total;
@@ -103,6 +110,8 @@ struct sph_ctx {
     unsigned long long *rowstart = nullptr, *pool_used = nullptr;  // pool_used: [reserved, listed]
     uint32_t* rowcap = nullptr;    // row-length hints in the current sorted order
     int* hint_ok = nullptr;        // device flag: cnt holds row lengths of the current order
+    bool cnt_valid = false;        // host: cnt holds the row lengths of the current order
+    uint32_t* cnt_orig = nullptr;  // row lengths carried to the caller's order (set_particles)
     uint64_t* scan64 = nullptr;
     bool canon_valid = false;      // off / col_plain hold the canonical CSR
     int64_t col_plain_cap = 0;
@@ -616,6 +625,7 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
     ctx->radix_passes = (kPatchShift + bits + 7) / 8;
     ctx->patch_off.assign(offsets, offsets + np + 1);
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = ctx->sup_valid = false;
+    ctx->cnt_valid = false;
     destroy_graphs(ctx);
     // new particle order: no row-length hints
     CK(cudaMemsetAsync(ctx->hint_ok, 0, sizeof(int), ctx->stream));
@@ -809,7 +819,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         double** g[14] = {&f.vhx, &f.vhy, &f.vhz, &f.rho, &f.P, &f.c, &f.A, &f.hc, &f.invh, &f.ax, &f.ay, &f.az, &f.du, nullptr};
         for (int k = 0; k < 13 && ok; k++) ok = dalloc(ctx, *g[k], N);
     }
-    ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->nown, N) && dalloc(ctx, ctx->off, N + 1) &&
+    ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->cnt_orig, N) && dalloc(ctx, ctx->nown, N) &&
+         dalloc(ctx, ctx->off, N + 1) &&
          dalloc(ctx, ctx->col, (size_t)ctx->pool_cap) && dalloc(ctx, ctx->rowcap, N);
     ctx->cap_units = ctx->cap_n / 32 + ctx->cap_patch + 1;
     ok = ok && dalloc(ctx, ctx->rowstart, N) && dalloc(ctx, ctx->pool_used, 2) && dalloc(ctx, ctx->hint_ok, 1) &&
@@ -868,6 +879,15 @@ sph_status sph_set_particles(sph_ctx* ctx, int64_t n, const double* x, const dou
     if (n > 0)
         for (int k = 0; k < 9; k++)
             if (!src[k]) return fail(ctx, SPH_EINVAL, "NULL field pointer");
+    // the same number of particles again (one patch): the last lists' row
+    // lengths, carried to the caller's order, reserve the rows of the first
+    // search on the new particles (a set uploaded again keeps its rows; for
+    // any other set they are only a poorer guess, which the search repairs)
+    const bool carry = ctx->cnt_valid && n == ctx->n && n > 0 && ctx->npatch == 1;
+    if (carry) {
+        const int grid = (int)((n + 255) / 256 < ctx->sms * 16 ? (n + 255) / 256 : ctx->sms * 16);
+        k_scatter_u32<<<grid, 256, 0, ctx->stream>>>(n, ctx->cnt, ctx->perm[ctx->cur], ctx->cnt_orig);
+    }
     ctx->cur = 0;
     State& s = ctx->st[0];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -883,6 +903,12 @@ sph_status sph_set_particles(sph_ctx* ctx, int64_t n, const double* x, const dou
     int64_t offs[2] = {0, n};
     st = setup_patches(ctx, 1, offs);
     if (st != SPH_OK) return st;
+    if (carry) {
+        CK(cudaMemcpyAsync(ctx->cnt, ctx->cnt_orig, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream));
+        ctx->cnt_valid = true;
+    }
     ctx->fresh = true;
     ctx->nnz = -1;
     st = check_status(ctx, "sph_set_particles");
@@ -933,6 +959,7 @@ sph_status sph_find_neighbors(sph_ctx* ctx)
     ctx->nnz = (int64_t)nnz;
     if (st != SPH_OK) return st;
     ctx->nb_valid = true;
+    ctx->cnt_valid = true;
     if (reuse) {
         ctx->sup_valid = true;
         if (rebuild) ctx->rebuilds++;
@@ -1079,6 +1106,7 @@ sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last)
     st = check_status(ctx, "sph_step");
     ctx->nb_valid = false;
     ctx->rho_valid = ctx->acc_valid = (st == SPH_OK);
+    ctx->cnt_valid = st == SPH_OK;
     if (st != SPH_OK) return st;
     if (dt_last) {
         CK(cudaMemcpy(dt_last, &ctx->pd[0].dt, sizeof(double), cudaMemcpyDeviceToHost));
@@ -1347,7 +1375,9 @@ sph_status sph_autotune(sph_ctx* ctx)
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = ctx->sup_valid = false;
     st = after_launches(ctx, "sph_autotune");
     if (st != SPH_OK) return st;
-    return check_status(ctx, "sph_autotune");
+    st = check_status(ctx, "sph_autotune");
+    ctx->cnt_valid = st == SPH_OK;   // the last timed search's rows, in the current order
+    return st;
 }
 
 sph_status sph_get_tuning(sph_ctx* ctx, int32_t* tpp, double* cell_factor)
