@@ -291,6 +291,7 @@ def main():
         sim.autotune()
         sim.step(1)
     tpp, cf = binding.sph_get_tuning(sim.ctx)
+    tpp_den = binding.sph_get_density_tpp(sim.ctx)
     mode = sim.pair_mode()
     torch.cuda.synchronize()
     sim.pair_count(reset=True)
@@ -407,7 +408,8 @@ def main():
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
-                   "threads_per_particle": tpp, "cell_factor": cf, "pair_mode": mode,
+                   "threads_per_particle": tpp, "threads_per_particle_density": tpp_den,
+                   "cell_factor": cf, "pair_mode": mode,
                    "list_skin": args.skin, "searches_in_timed_steps": rebuilds if args.skin > 0 else args.steps,
                    "timed": "K steps with CUDA events between phases (no graph)"},
         "steps_per_s": steps_per_s, "pairs_per_step": pairs_per_step,
@@ -422,7 +424,7 @@ def main():
     # the other pair mode at the same cell factor (and lanes per particle)
     if args.mode_steps > 0 and world == 1:
         other = "fused" if mode == "lists" else "lists"
-        sim.close()
+        # a second context beside the tuned one (both fit in HBM)
         so = make(args.precision, pair_mode=other, cell_factor=cf, threads_per_particle=tpp)
         for _ in range(args.warmup):
             so.step(1)
@@ -446,7 +448,6 @@ def main():
                                    "ms_per_step": mso, "steps": args.mode_steps, "cell_factor": cf,
                                    "threads_per_particle": tpp,
                                    "phase_ms_per_step": {k: v[0] / args.mode_steps for k, v in profo.items()}}
-        sim = make(args.precision, pair_mode=mode, cell_factor=cf, threads_per_particle=tpp)
 
     # FP64 GPU path on the same patch
     if args.fp64_steps > 0 and args.precision == "mixed":

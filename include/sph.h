@@ -243,8 +243,13 @@ sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes);
  * particles and keeps the fastest; the particle state is left unchanged. */
 sph_status sph_autotune(sph_ctx* ctx);
 
-/* Current launch configuration (after sph_autotune or as configured). */
+/* Current launch configuration (after sph_autotune or as configured): the
+ * momentum sum's lanes per particle and the cell factor. */
 sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* cell_factor);
+
+/* Lanes per particle of the density sum (sph_autotune tunes it apart from the
+ * momentum sum's). */
+sph_status sph_get_density_tpp(sph_ctx* ctx, int32_t* threads_per_particle);
 
 /* The pair mode in effect: SPH_PAIRS_LISTS or SPH_PAIRS_FUSED (SPH_PAIRS_AUTO
  * resolves to one of them in sph_autotune). */

@@ -79,6 +79,7 @@ SIGNATURES = {
     "sph_autotune": (_ST, [_P]),
     "sph_get_tuning": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
     "sph_get_pair_mode": (_ST, [_P, ctypes.POINTER(_I32)]),
+    "sph_get_density_tpp": (_ST, [_P, ctypes.POINTER(_I32)]),
     "sph_get_list_rebuilds": (_ST, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "sph_set_profiling": (_ST, [_P, ctypes.c_int]),
     "sph_get_profile": (_ST, [_P, _P, _P, _I32]),
@@ -280,6 +281,13 @@ def sph_get_pair_mode(ctx):
     m = ctypes.c_int32()
     _check(ctx, lib().sph_get_pair_mode(ctx, ctypes.byref(m)))
     return "fused" if m.value == SPH_PAIRS_FUSED else "lists"
+
+
+def sph_get_density_tpp(ctx):
+    """Lanes per particle of the density sum."""
+    v = ctypes.c_int32()
+    _check(ctx, lib().sph_get_density_tpp(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def sph_get_list_rebuilds(ctx):

@@ -78,7 +78,8 @@ struct sph_ctx {
     int cap_patch = 0, cap_items = 0;
     int64_t n = 0;
     int npatch = 0, nitems = 0, radix_passes = 3;
-    int tpp_pair = 8;
+    int tpp_pair = 8;              // lanes per particle of the momentum sum
+    int tpp_den = 8;               // ... and of the density sum
     double cell_factor = 0.5;
     int mixed = 1;
     bool fused = false;            // pair sums without lists (SPH_PAIRS_FUSED in effect)
@@ -431,7 +432,7 @@ void enqueue_density(sph_ctx* ctx)
         return;
     }
     Phase p(ctx, SPH_PHASE_DENSITY);
-    ctx->launches += launch_density(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
+    ctx->launches += launch_density(launch_of(ctx), pair_args(ctx), ctx->tpp_den, ctx->mixed);
 }
 
 void enqueue_momentum(sph_ctx* ctx)
@@ -768,7 +769,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ctx->mixed = cfg.precision == SPH_MIXED;
     ctx->kernel_b = kernel_norm(cfg.kernel, cfg.kernel_n);
     ctx->cell_factor = cfg.cell_factor;
-    if (t) ctx->tpp_pair = t;
+    if (t) ctx->tpp_pair = ctx->tpp_den = t;
     ctx->fused = cfg.pair_mode == SPH_PAIRS_FUSED;
     ctx->cap_n = cfg.max_particles;
     ctx->cap_patch = cfg.max_patches;
@@ -1333,26 +1334,35 @@ sph_status sph_autotune(sph_ctx* ctx)
     const bool try_lists = ctx->cfg.pair_mode != SPH_PAIRS_FUSED;
     const bool try_fused = ctx->cfg.pair_mode != SPH_PAIRS_LISTS;
     double best_total = 1e300, best_f = ctx->cell_factor;
-    int best_pair = ctx->tpp_pair;
+    int best_pair = ctx->tpp_pair, best_den = ctx->tpp_den;
     bool best_fused = ctx->fused;
     for (double f : factors) {
         ctx->cell_factor = f;
         enqueue_sort(ctx);
         if (try_lists) {
             ctx->fused = false;
-            float bpair = 1e30f;
-            int tpair = 8;
+            float bden = 1e30f, bmom = 1e30f;
+            int tden = 8, tmom = 8;
             const float bnb = timeit([&] { enqueue_lists(ctx); });
+            // the two sums separately (the momentum sum reads the density's records)
+            for (int t : pair_tpps) {
+                ctx->tpp_den = t;
+                const float ms = timeit([&] { enqueue_density(ctx); });
+                if (ms < bden) { bden = ms; tden = t; }
+            }
+            ctx->tpp_den = tden;
+            enqueue_density(ctx);
             for (int t : pair_tpps) {
                 ctx->tpp_pair = t;
-                float ms = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
-                if (ms < bpair) { bpair = ms; tpair = t; }
+                const float ms = timeit([&] { enqueue_momentum(ctx); });
+                if (ms < bmom) { bmom = ms; tmom = t; }
             }
-            const double tot = (double)bnb + (double)bpair;
+            const double tot = (double)bnb + (double)bden + (double)bmom;
             if (tot < best_total) {
                 best_total = tot;
                 best_f = f;
-                best_pair = tpair;
+                best_pair = tmom;
+                best_den = tden;
                 best_fused = false;
             }
         }
@@ -1370,6 +1380,7 @@ sph_status sph_autotune(sph_ctx* ctx)
     cudaEventDestroy(e1);
     ctx->cell_factor = best_f;
     ctx->tpp_pair = best_pair;
+    ctx->tpp_den = best_den;
     ctx->fused = best_fused;
     ctx->prof = prof0;
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = ctx->sup_valid = false;
@@ -1385,6 +1396,13 @@ sph_status sph_get_tuning(sph_ctx* ctx, int32_t* tpp, double* cell_factor)
     if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
     if (tpp) *tpp = ctx->tpp_pair;
     if (cell_factor) *cell_factor = ctx->cell_factor;
+    return SPH_OK;
+}
+
+sph_status sph_get_density_tpp(sph_ctx* ctx, int32_t* tpp)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    if (tpp) *tpp = ctx->tpp_den;
     return SPH_OK;
 }
 
