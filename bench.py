@@ -76,6 +76,18 @@ def rank_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def reduce_over_ranks(ms, pairs, device):
+    """Replicas (one independent patch per rank, no data-path collective):
+    the job's time is the slowest rank's, its pairs every rank's."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -338,12 +350,7 @@ def main():
     ms_graph = g0.elapsed_time(g1)
     pairs_graph = sim.pair_count(reset=True)
     if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-        p = torch.tensor([pairs], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(p, op=torch.distributed.ReduceOp.SUM)
-        pairs_all = float(p.item())
+        ms_total, pairs_all = reduce_over_ranks(ms_total, pairs, dev)
     else:
         pairs_all = float(pairs)
     sec = ms_total / 1e3
