@@ -68,6 +68,9 @@ WORKLOADS = {
     "c1": ("square patch 20^3 (8,000 particles), omega=5", 20),
     "c2": ("square patch 100^3 (1,000,000 particles), omega=5", 100),
     "c3": ("square patch 200^3 (8,000,000 particles), omega=5", 200),
+    "c4": ("64 independent square patches, edges 10..60, omega 2..8 (seed 0), one launch per phase", None),
+    "c5": ("irregular patch 159^3 (4,019,679 particles): jittered lattice, log-normal masses, "
+           "neighbour counts 50-400", 159),
 }
 
 
@@ -242,6 +245,8 @@ def main():
     ap.add_argument("--pair-mode", default="auto", choices=["auto", "lists", "fused"],
                     help="pair sums over neighbour lists, list-free (the search inside the sums), "
                          "or whichever the autotuner finds faster")
+    ap.add_argument("--adapt-h", type=int, choices=[0, 1], default=None,
+                    help="h adaptation (default: on, off for c5, which is timed with h frozen)")
     ap.add_argument("--skin", type=float, default=0.0,
                     help="reuse the neighbour search across steps: search radius scaled by 1 + skin, "
                          "exact lists filtered from it every step (0: search every step)")
@@ -273,22 +278,31 @@ def main():
     from paper_1905_03344_gb300 import binding, build, inputs
     build.build()
     wl, n_edge = WORKLOADS[args.config]
-    f = inputs.square_patch(n_edge)
+    offsets = None
+    if args.config == "c4":
+        f, offsets, _, _ = inputs.batch_patches(64, seed=0)
+    elif args.config == "c5":
+        f = inputs.irregular_patch(159)
+    else:
+        f = inputs.square_patch(n_edge)
+    adapt = args.adapt_h if args.adapt_h is not None else (0 if args.config == "c5" else 1)
     n = len(f["x"])
     stream = torch.cuda.current_stream()
     dfields = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in f.items()}
 
     def make(precision, graph=False, **over):
         kw = {"kernel": args.kernel, "kernel_n": 6, "grad_h": int(args.grad_h), "pair_mode": args.pair_mode,
-              "list_skin": args.skin}
+              "list_skin": args.skin, "adapt_h": adapt}
         if args.cell_factor:
             kw["cell_factor"] = args.cell_factor
         if args.tpp:
             kw["threads_per_particle"] = args.tpp
         kw.update(over)
-        sim = binding.SPH(n, precision=precision, stream=stream.cuda_stream,
-                          use_graph=int(graph), max_pairs=int(160 * n), **kw)
+        sim = binding.SPH(n, precision=precision, stream=stream.cuda_stream, use_graph=int(graph),
+                          max_pairs=int(160 * n), max_patches=64 if offsets is not None else 1, **kw)
         sim.set_particles(dfields)
+        if offsets is not None:
+            sim.set_patches(offsets)
         return sim
 
     # FP32 FMA rate of this GPU (0.3 s, before anything is timed)
@@ -411,6 +425,7 @@ def main():
         if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": wl, "particles": n, "precision": args.precision, "kernel": args.kernel,
+                   "adapt_h": bool(adapt),
                    "grad_h": bool(args.grad_h),
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
@@ -507,6 +522,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             sim.set_particles(hfields)
+            if offsets is not None:
+                sim.set_patches(offsets)
             sim.step(1)
             sim.conserved()
         el = time.perf_counter() - t0
@@ -517,7 +534,8 @@ def main():
                        "call": "sph_set_particles(host) + sph_step(1) + sph_conserved per step"}
     sim.close()
 
-    if rank == 0 and world == 1 and not args.no_cpu:
+    # the oracle baseline is of the square patch (c1-c3)
+    if rank == 0 and world == 1 and not args.no_cpu and args.config in ("c1", "c2", "c3"):
         line["cpu_baseline"] = cpu_baseline(args)
         line["cpu_baseline_1core"] = cpu_baseline_1thread(args)
         try:
