@@ -101,8 +101,9 @@ struct MomSink {
         const uint32_t cws[4] = {q[32 * (head & (kQueue - 1))], q[32 * ((head + 1) & (kQueue - 1))],
                                  q[32 * ((head + 2) & (kQueue - 1))], q[32 * ((head + 3) & (kQueue - 1))]};
         float bx, by, bz, bu;
-        if (zmode) momentum_chunk<1, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu);
-        else momentum_chunk<0, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu);
+        const GlobalRecs R{src};
+        if (zmode) momentum_chunk<1, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, R);
+        else momentum_chunk<0, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, R);
         mom_acc_add(A, bx, by, bz, bu);
         head += nv;
     }

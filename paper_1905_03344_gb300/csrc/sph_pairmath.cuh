@@ -517,19 +517,30 @@ __device__ __forceinline__ void density_finish(const PairArgs& a, int64_t i, flo
 #define SPH_MOM_PACK 1                  // two pairs at once in packed FP32x2 arithmetic
 #endif
 
+// the records of pair u of a chunk straight from the record arrays
+struct GlobalRecs {
+    const PairSrc& src;
+    __device__ __forceinline__ void load(int, uint32_t cw, float4& q, float4& v, float4& t) const
+    {
+        const uint32_t j = cw & kColMask;
+        q = src.r5[j];
+        v = src.rv[j];
+        t = src.rt[j];
+    }
+};
+
 // momentum: the plain sums (bx, by, bz, bu) of up to four pairs, the column
-// words cws[0 .. nv)
-template <int ZW, int KERN, bool GH>
+// words cws[0 .. nv), the records of pair u from R.load(u, ...)
+template <int ZW, int KERN, bool GH, class Recs4 = GlobalRecs>
 __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4* tab, const PairSide& I,
                                                const float4& vi, const float4& ti, float wi5, const MomConst& K,
                                                int kn, const uint32_t (&cws)[4], uint32_t nv, float& bx, float& by,
-                                               float& bz, float& bu)
+                                               float& bz, float& bu, const Recs4& R)
 {
     bx = by = bz = bu = 0.0f;
-#if SPH_MOM_PACK
     // packed pairs: the Wendland kernel in the symmetrised form (the Sinc
     // kernel and the grad-h form take the scalar loop)
-    if (KERN == SPH_KERNEL_WENDLAND && !GH) {
+    if constexpr (SPH_MOM_PACK && KERN == SPH_KERNEL_WENDLAND && !GH) {
         float2 px = p2(0.0f), py = p2(0.0f), pz = p2(0.0f), pu = p2(0.0f);
 #pragma unroll
         for (int hh = 0; hh < 2; hh++) {
@@ -537,10 +548,9 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
             if (ua >= nv) break;
             const bool hb = ua + 1u < nv;
             const uint32_t cwa = cws[2 * hh], cwb = hb ? cws[2 * hh + 1] : cwa;
-            const uint32_t ja = cwa & kColMask, jb = cwb & kColMask;
-            const float4 qa = src.r5[ja], qb = src.r5[jb];
-            const float4 va = src.rv[ja], vb = src.rv[jb];
-            const float4 ta = src.rt[ja], tb = src.rt[jb];
+            float4 qa, qb, va, vb, ta, tb;
+            R.load(2 * hh, cwa, qa, va, ta);
+            R.load(hb ? 2 * hh + 1 : 2 * hh, cwb, qb, vb, tb);
             float dxa, dya, dza, dxb, dyb, dzb;
             col_dx<ZW>(src, tab, I, cwa, qa, dxa, dya, dza);
             col_dx<ZW>(src, tab, I, cwb, qb, dxb, dyb, dzb);
@@ -555,24 +565,21 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
         by = py.x + py.y;
         bz = pz.x + pz.y;
         bu = pu.x + pu.y;
-        return;
-    }
-#endif
+    } else {
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-        if ((uint32_t)u >= nv) break;
-        const uint32_t cw = cws[u];
-        const uint32_t j = cw & kColMask;
-        const float4 q = src.r5[j];
-        const float4 vj = src.rv[j];
-        const float4 tj = src.rt[j];
-        float dx, dy, dz;
-        col_dx<ZW>(src, tab, I, cw, q, dx, dy, dz);
-        const PairTerms t = momentum_pair<KERN, GH>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
-        bx += t.ax;
-        by += t.ay;
-        bz += t.az;
-        bu += t.du;
+        for (int u = 0; u < 4; u++) {
+            if ((uint32_t)u >= nv) break;
+            const uint32_t cw = cws[u];
+            float4 q, vj, tj;
+            R.load(u, cw, q, vj, tj);
+            float dx, dy, dz;
+            col_dx<ZW>(src, tab, I, cw, q, dx, dy, dz);
+            const PairTerms t = momentum_pair<KERN, GH>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
+            bx += t.ax;
+            by += t.ay;
+            bz += t.az;
+            bu += t.du;
+        }
     }
 }
 

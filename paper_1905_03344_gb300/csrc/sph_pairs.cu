@@ -164,7 +164,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         const uint32_t cws[4] = {w.x, w.y, w.z, w.w};
         const uint32_t nv = min(len - ch * 4u, 4u);
         float bx, by, bz, bu;
-        momentum_chunk<ZW, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu);
+        momentum_chunk<ZW, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, GlobalRecs{src});
         mom_acc_add(A, bx, by, bz, bu);
         w = wn;
     }
