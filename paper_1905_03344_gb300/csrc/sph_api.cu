@@ -817,8 +817,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
              dalloc(ctx, ctx->rec.acc, N);
     } else {
         Fp64& f = ctx->f64;
-        double** g[14] = {&f.vhx, &f.vhy, &f.vhz, &f.rho, &f.P, &f.c, &f.A, &f.hc, &f.invh, &f.ax, &f.ay, &f.az, &f.du, nullptr};
-        for (int k = 0; k < 13 && ok; k++) ok = dalloc(ctx, *g[k], N);
+        double** g[14] = {&f.vhx, &f.vhy, &f.vhz, &f.rho, &f.P, &f.c, &f.A, &f.hc, &f.w, &f.w5, &f.ax, &f.ay, &f.az, &f.du};
+        for (int k = 0; k < 14 && ok; k++) ok = dalloc(ctx, *g[k], N);
     }
     ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->cnt_orig, N) && dalloc(ctx, ctx->nown, N) &&
          dalloc(ctx, ctx->off, N + 1) &&

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_FUSED_DEN_MINB)
         uint32_t cnt = 0;
         if (i < U.end) {
             const bool big = i >= P->end - (int64_t)P->nbig;
-            DensSinkD<KERN, GH> s = {&pa, pa.s.x[i], pa.s.y[i], pa.s.z[i], 0.5 * pa.f.invh[i], P->lz,
+            DensSinkD<KERN, GH> s = {&pa, pa.s.x[i], pa.s.y[i], pa.s.z[i], pa.f.w[i], P->lz,
                                      pa.kernel_n, 0.0, 0.0, 0u, 0u};
             walk_all<DensSinkD<KERN, GH>, K>(a, P, i, big, s);
             density_finish_fp64<GH>(pa, i, s.sum, s.sumd);

@@ -126,7 +126,8 @@ struct Recs {             // FP32 records (written by gather / density)
 
 struct Fp64 {             // FP64-path fields
     double *vhx, *vhy, *vhz;   // time-centred velocity
-    double *rho, *P, *c, *A, *hc, *invh;
+    double *rho, *P, *c, *A, *hc;
+    double *w, *w5;            // w = 1/(2h) and w^5 of the kernel gradient
     double *ax, *ay, *az, *du;
 };
 

@@ -670,8 +670,8 @@ __device__ __forceinline__ SideD side_fp64(const PairArgs& a, const PatchDev* P,
     I.vy = a.f.vhy[i];
     I.vz = a.f.vhz[i];
     I.h = a.s.h[i];
-    I.w = 0.5 * a.f.invh[i];
-    I.w5 = I.w * I.w * I.w * I.w * I.w;
+    I.w = a.f.w[i];
+    I.w5 = a.f.w5[i];
     I.rho = a.f.rho[i];
     I.A = a.f.A[i];
     I.c = a.f.c[i];
@@ -691,16 +691,18 @@ __device__ __forceinline__ PairTermsD momentum_pair_fp64(const PairArgs& a, cons
     pair_dx_fp64(a.s, I.x, I.y, I.z, j, I.lz, dx, dy, dz);
     const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
     const double r = sqrt(r2);
-    const double wj = 0.5 * a.f.invh[j];
-    const double fi = KernF<KERN>::grad(r, I.w, I.w5, kn), fj = KernF<KERN>::grad(r, wj, wj * wj * wj * wj * wj, kn);
+    const double fi = KernF<KERN>::grad(r, I.w, I.w5, kn), fj = KernF<KERN>::grad(r, a.f.w[j], a.f.w5[j], kn);
     const double F = __dadd_rn(fi, fj);   // not contracted with either product
     const double vx = I.vx - a.f.vhx[j], vy = I.vy - a.f.vhy[j], vz = I.vz - a.f.vhz[j];
     const double vdot = fma(vx, dx, fma(vy, dy, vz * dz));
     double pi_ = 0.0;
     if (vdot < 0.0) {
+        // Pi = mu (beta mu - alpha cbar) / rhobar with mu = N / D, N = hbar v.x,
+        // D = r^2 + eps hbar^2, as one division: N (beta N - alpha cbar D) / (D^2 rhobar)
         const double hbar = 0.5 * (I.h + a.s.h[j]);
-        const double mu = hbar * vdot / fma(a.eps * hbar, hbar, r2);
-        pi_ = fma(-a.alpha * 0.5 * (I.c + a.f.c[j]), mu, a.beta * mu * mu) / (0.5 * (I.rho + a.f.rho[j]));
+        const double N = hbar * vdot, D = fma(a.eps * hbar, hbar, r2);
+        const double cbar = 0.5 * (I.c + a.f.c[j]), rhobar = 0.5 * (I.rho + a.f.rho[j]);
+        pi_ = N * fma(a.beta, N, -a.alpha * cbar * D) / (D * D * rhobar);
     }
     const double mj = a.s.m[j];
     PairTermsD t;

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
         const PatchDev* P = a.pd + a.patch_of[i];
         const double xi = a.s.x[i], yi = a.s.y[i], zi = a.s.z[i];
-        const double w = 0.5 * a.f.invh[i];
+        const double w = a.f.w[i];
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
         double sum = 0.0, sumd = 0.0;

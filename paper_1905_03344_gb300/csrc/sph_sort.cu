@@ -590,7 +590,9 @@ __device__ __forceinline__ void write_records(int64_t k, const PatchDev* P, uint
         f.vhx[k] = vhx;
         f.vhy[k] = vhy;
         f.vhz[k] = vhz;
-        f.invh[k] = 1.0 / h;
+        const double w = 0.5 / h;
+        f.w[k] = w;
+        f.w5[k] = w * w * w * w * w;
     }
 }
 
