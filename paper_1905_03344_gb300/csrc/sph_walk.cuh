@@ -57,11 +57,13 @@ static __device__ __noinline__ int exact_pair_at(const NbArgs& a, int64_t i, uin
 #define SPH_NB_MINB 8                   // resident CTAs per SM the registers are sized for
 #endif
 #ifndef SPH_NB_GROUP
-#define SPH_NB_GROUP 4                  // candidates loaded together per lane
+#define SPH_NB_GROUP 4                  // candidates loaded together per lane (1-5)
 #endif
 constexpr int kNbtWarps = 4;            // warps per CTA
 constexpr int kGroup = SPH_NB_GROUP;
-static_assert(kGroup >= 1 && kGroup <= 8, "a group may fill at most one half of the ring");
+// at most one half of the list ring; the list-free sums' pair queue (eight
+// slots) takes a group and three pairs left over, so groups stop at 5
+static_assert(kGroup >= 1 && kGroup <= 5, "a group must fit the list ring and the pair queue");
 constexpr int kRing = 16;               // ring slots per lane (two halves of 8)
 constexpr uint32_t kHintMargin = 8;     // growth a row may have since the hint, beyond c/3
 
