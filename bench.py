@@ -305,7 +305,7 @@ def main():
             sim.set_patches(offsets)
         return sim
 
-    # FP32 FMA rate of this GPU (0.3 s, before anything is timed)
+    # FMA rate of this GPU in the path's precision (0.3 s, before anything is timed)
     fma_peak = binding.sph_fma_peak("fp64" if args.precision == "fp64" else "mixed",
                                     stream=stream.cuda_stream) / 1e12
 
@@ -379,8 +379,17 @@ def main():
     flops_pair = {(False, False): FLOPS_PER_PAIR_MOMENTUM, (True, False): FLOPS_PER_PAIR_MOMENTUM_SINC,
                   (False, True): FLOPS_PER_PAIR_MOMENTUM_GRADH,
                   (True, True): FLOPS_PER_PAIR_MOMENTUM_SINC_GRADH}[(args.kernel == "sinc", args.grad_h)]
-    mom_tf = flops_pair * pairs_per_step / (mom_ms / 1e3) / 1e12
     prec_tag = "mixed" if args.precision == "mixed" else "fp64"
+    pair_peak = fp32_peak
+    pair_peak_src = "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)" % (SMS, FP32_LANES_PER_SM, sm_max)
+    if args.precision == "fp64":
+        # the FP64 pair sums run on the FP64 pipe: their own operation count
+        # (the Wendland form; no count is kept for the others) against the
+        # measured FP64 FMA rate
+        flops_pair = FLOPS_PER_PAIR_MOMENTUM_FP64 if args.kernel == "wendland" and not args.grad_h else None
+        pair_peak = fma_peak
+        pair_peak_src = "measured: sph_fma_peak FP64 FMA chains"
+    mom_tf = flops_pair * pairs_per_step / (mom_ms / 1e3) / 1e12 if flops_pair else None
     if mode == "lists":
         # dominant kernel: the neighbour-list search (k_nb_thread), HBM roofline
         # on its algorithmic bytes
@@ -397,24 +406,22 @@ def main():
         # list-free: the momentum pass (search + pair sums) dominates; its pair
         # arithmetic against the FP32 peak (the search is not counted)
         roof = {"bound": "alu", "kernel": "k_fused_momentum_" + prec_tag, "achieved": mom_tf,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak, "traffic": None,
-                "flops_per_pair": flops_pair, "ms_per_launch": mom_ms,
-                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
-                               % (SMS, FP32_LANES_PER_SM, sm_max),
+                "peak": pair_peak, "unit": "TFLOP/s", "frac": mom_tf and mom_tf / pair_peak, "traffic": None,
+                "flops_per_pair": flops_pair, "ms_per_launch": mom_ms, "peak_source": pair_peak_src,
                 "share_of_step": prof["momentum"][0] / ms_total}
-    # the pair sums: FP32 pipe (mixed) against the derived FP32 peak
+    # the pair sums: FP32 pipe (mixed) against the derived FP32 peak, FP64
+    # pipe (FP64 path) against the measured FP64 FMA rate
     roof_mom = {"bound": "alu", "kernel": ("k_momentum_" if mode == "lists" else "k_fused_momentum_") + prec_tag,
-                "achieved": mom_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mom_tf / fp32_peak,
+                "achieved": mom_tf, "peak": pair_peak, "unit": "TFLOP/s", "frac": mom_tf and mom_tf / pair_peak,
                 # the DRAM figure is the standard Wendland variant's
                 "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step)
                 if MOMENTUM_DRAM_BYTES_PER_ENTRY and args.kernel == "wendland" and not args.grad_h
-                and mode == "lists" else None,
-                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
-                               % (SMS, FP32_LANES_PER_SM, sm_max),
-                "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf / fma_peak,
+                and mode == "lists" and args.precision == "mixed" else None,
+                "peak_source": pair_peak_src,
+                "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf and mom_tf / fma_peak,
                 "flops_per_pair": flops_pair, "ms_per_launch": mom_ms,
                 "share_of_step": prof["momentum"][0] / ms_total}
-    if clk.get("sm_mhz"):
+    if clk.get("sm_mhz") and mom_tf and args.precision == "mixed":
         roof_mom["frac_at_sampled_clock"] = mom_tf / (fp32_peak * clk["sm_mhz"] / sm_max)
 
     line = {
