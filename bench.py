@@ -153,61 +153,66 @@ def oracle_kw(args):
     return {"kernel": args.kernel, "kernel_n": 6, "grad_h": bool(args.grad_h)}
 
 
-def cpu_baseline_1thread(args, sample_n=40, nsteps=1):
-    """The same oracle step on one host core, on the 40^3 patch."""
+def oracle_sample(args, threads, n_edge, warmup=3, nsteps=None, min_seconds=10.0):
+    """The FP64 oracle (as it stands) on the n_edge^3 square patch, stepped
+    with the timestep of the benchmarked patch: the first Courant step
+    C min(h/c) taken with the full-size patch's h (dt follows h), held fixed.
+    The sample's steps then cover the same stretch of the flow as the
+    full-size steps (with its own Courant step a smaller patch would run ahead
+    in time, into states where the oracle's uniform grid, sized by the largest
+    h, is slower).  After `warmup` untimed steps, times `nsteps` steps, or as
+    many as fill `min_seconds`.  Returns (pairs, seconds, steps, n_edge, dt)."""
+    import numpy as np
     import oracle
     from paper_1905_03344_gb300 import inputs
-    f = inputs.square_patch(sample_n)
-    sim = oracle.Sim(f, nthreads=1, **oracle_kw(args))
+    full = WORKLOADS[args.config][1] or 200
+    n_edge = min(n_edge, full)
+    f = inputs.square_patch(n_edge)
+    gamma = inputs.GAMMA
+    # c = sqrt(gamma P / rho) with P = (gamma - 1) rho u, and h = eta L / n
+    cmax = float(np.sqrt(gamma * (gamma - 1.0) * f["u"]).max())
+    dt = 0.2 * inputs.ETA / full / cmax
+    sim = oracle.Sim(f, nthreads=threads, dt_fixed=dt, **oracle_kw(args))
+    for _ in range(warmup):
+        sim.step(1)
     t0 = time.perf_counter()
     pairs = 0
-    for _ in range(nsteps):
+    k = 0
+    while True:
         sim.step(1)
         pairs += sim.nnz
-    dt = time.perf_counter() - t0
+        k += 1
+        el = time.perf_counter() - t0
+        if (nsteps is not None and k >= nsteps) or (nsteps is None and el >= min_seconds):
+            return pairs, el, k, n_edge, dt
+
+
+def cpu_baseline_1thread(args, sample_n=40):
+    """The same oracle steps on one host core, on the 40^3 patch."""
+    pairs, dt, k, ne, step_dt = oracle_sample(args, 1, sample_n, min_seconds=5.0)
     return {"value": 2.0 * pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d full oracle step(s) on the %d^3 square patch (%d particles), one host core; %.1f s"
-                      % (nsteps, sample_n, sample_n ** 3, dt)}
+            "sample": "%d full oracle steps on the %d^3 square patch (%d particles) after 3 warm-up steps, "
+                      "dt = %.3g (the full-size patch's Courant step), one host core; %.1f s"
+                      % (k, ne, ne ** 3, step_dt, dt)}
 
 
-def cpu_baseline(args, sample_n=100, nsteps=1):
-    """The FP64 oracle (as it stands) on host cores, one full step on the
-    100^3 patch: the same rotating-patch workload at 1/8 of the particles."""
-    import oracle
-    from paper_1905_03344_gb300 import inputs
-    f = inputs.square_patch(sample_n)
+def cpu_baseline(args, sample_n=100):
+    """The FP64 oracle (as it stands) on all host cores: full steps on the
+    100^3 patch, the same rotating-patch workload at 1/8 of the particles."""
     threads = os.cpu_count() or 1
-    sim = oracle.Sim(f, nthreads=threads, **oracle_kw(args))
-    t0 = time.perf_counter()
-    pairs = 0
-    for _ in range(nsteps):
-        sim.step(1)
-        pairs += sim.nnz
-    dt = time.perf_counter() - t0
+    pairs, dt, k, ne, step_dt = oracle_sample(args, threads, sample_n)
     return {"value": 2.0 * pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d full oracle step(s) (neighbours..update) on the %d^3 square patch "
-                      "(%d particles), OpenMP on all host cores; %.1f s" % (nsteps, sample_n,
-                                                                            sample_n ** 3, dt)}
+            "sample": "%d full oracle steps (neighbours..update) on the %d^3 square patch (%d particles) "
+                      "after 3 warm-up steps, dt = %.3g (the full-size patch's Courant step), OpenMP on "
+                      "all host cores; %.1f s" % (k, ne, ne ** 3, step_dt, dt)}
 
 
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return 0
-    import oracle
-    from paper_1905_03344_gb300 import inputs
-    n_edge = 100
-    f = inputs.square_patch(n_edge)
     threads = os.cpu_count() or 1
-    sim = oracle.Sim(f, nthreads=threads, **oracle_kw(args))
-    for _ in range(args.warmup):
-        sim.step(1)
-    t0 = time.perf_counter()
-    pairs = 0
-    for _ in range(args.steps):
-        sim.step(1)
-        pairs += sim.nnz
-    el = time.perf_counter() - t0
+    pairs, el, k, n_edge, step_dt = oracle_sample(args, threads, 50, warmup=args.warmup, nsteps=args.steps)
     val = 2.0 * pairs / el
     wl = WORKLOADS[args.config][0]
     line = {
@@ -220,8 +225,9 @@ def run_reference(args):
                    "sample": "%d^3 square patch per step" % n_edge},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "each step: one full FP64 oracle step on the %d^3 square patch "
-                                   "(%d particles), the %s workload at 1/8 of its particles"
-                                   % (n_edge, n_edge ** 3, args.config)},
+                                   "(%d particles) with the %s workload's Courant step (dt = %.3g), "
+                                   "so the steps span the same stretch of the flow"
+                                   % (n_edge, n_edge ** 3, args.config, step_dt)},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

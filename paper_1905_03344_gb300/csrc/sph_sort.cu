@@ -104,20 +104,29 @@ __global__ void k_reset_red(int npatch, PatchRed* red)
 // ---------------------------------------------------------------------------
 // A1a': per patch, a histogram of h / h_max in kHBins bins (integer counts,
 // so independent of the order of the atomics); it sets the class threshold.
+// Lanes of a warp that fall into the same bin (on a lattice, all of them)
+// add their count with one atomic.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_h_hist(State s, const WorkItem* items, int nitems, PatchRed* red)
 {
     __shared__ uint32_t hist[kHBins];
+    const int lane = threadIdx.x & 31;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         for (int b = threadIdx.x; b < kHBins; b += blockDim.x) hist[b] = 0u;
         __syncthreads();
         const double hmax = unord_f64(red[w.patch].hmax);
         const double scale = hmax > 0.0 ? (double)kHBins / hmax : 0.0;
-        for (int64_t i = w.begin + threadIdx.x; i < w.end; i += blockDim.x) {
-            const double t = s.h[i] * scale;
-            int b = t >= 0.0 && t < (double)kHBins ? (int)t : kHBins - 1;
-            atomicAdd(&hist[b], 1u);
+        // warp-uniform trip count (blockDim is a multiple of 32)
+        for (int64_t i0 = w.begin; i0 < w.end; i0 += blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;
+            int b = -1;
+            if (i < w.end) {
+                const double t = s.h[i] * scale;
+                b = t >= 0.0 && t < (double)kHBins ? (int)t : kHBins - 1;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, b);
+            if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[b], (uint32_t)__popc(peers));
         }
         __syncthreads();
         for (int b = threadIdx.x; b < kHBins; b += blockDim.x)
