@@ -153,7 +153,7 @@ def oracle_kw(args):
     return {"kernel": args.kernel, "kernel_n": 6, "grad_h": bool(args.grad_h)}
 
 
-def oracle_sample(args, threads, n_edge, warmup=3, nsteps=None, min_seconds=10.0):
+def oracle_sample(args, threads, n_edge, warmup=3, nsteps=None, min_seconds=10.0, max_steps=None):
     """The FP64 oracle (as it stands) on the n_edge^3 square patch, stepped
     with the timestep of the benchmarked patch: the first Courant step
     C min(h/c) taken with the full-size patch's h (dt follows h), held fixed.
@@ -161,7 +161,8 @@ def oracle_sample(args, threads, n_edge, warmup=3, nsteps=None, min_seconds=10.0
     full-size steps (with its own Courant step a smaller patch would run ahead
     in time, into states where the oracle's uniform grid, sized by the largest
     h, is slower).  After `warmup` untimed steps, times `nsteps` steps, or as
-    many as fill `min_seconds`.  Returns (pairs, seconds, steps, n_edge, dt)."""
+    many as fill `min_seconds` (at most `max_steps`).  Returns (pairs,
+    seconds, steps, n_edge, dt)."""
     import numpy as np
     import oracle
     from paper_1905_03344_gb300 import inputs
@@ -183,13 +184,16 @@ def oracle_sample(args, threads, n_edge, warmup=3, nsteps=None, min_seconds=10.0
         pairs += sim.nnz
         k += 1
         el = time.perf_counter() - t0
-        if (nsteps is not None and k >= nsteps) or (nsteps is None and el >= min_seconds):
+        if nsteps is not None:
+            if k >= nsteps:
+                return pairs, el, k, n_edge, dt
+        elif el >= min_seconds or (max_steps is not None and k >= max_steps):
             return pairs, el, k, n_edge, dt
 
 
 def cpu_baseline_1thread(args, sample_n=40):
     """The same oracle steps on one host core, on the 40^3 patch."""
-    pairs, dt, k, ne, step_dt = oracle_sample(args, 1, sample_n, min_seconds=5.0)
+    pairs, dt, k, ne, step_dt = oracle_sample(args, 1, sample_n, min_seconds=5.0, max_steps=max(args.steps, 1))
     return {"value": 2.0 * pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d full oracle steps on the %d^3 square patch (%d particles) after 3 warm-up steps, "
                       "dt = %.3g (the full-size patch's Courant step), one host core; %.1f s"
@@ -200,7 +204,7 @@ def cpu_baseline(args, sample_n=100):
     """The FP64 oracle (as it stands) on all host cores: full steps on the
     100^3 patch, the same rotating-patch workload at 1/8 of the particles."""
     threads = os.cpu_count() or 1
-    pairs, dt, k, ne, step_dt = oracle_sample(args, threads, sample_n)
+    pairs, dt, k, ne, step_dt = oracle_sample(args, threads, sample_n, max_steps=max(args.steps, 1))
     return {"value": 2.0 * pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d full oracle steps (neighbours..update) on the %d^3 square patch (%d particles) "
                       "after 3 warm-up steps, dt = %.3g (the full-size patch's Courant step), OpenMP on "
