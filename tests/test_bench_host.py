@@ -51,3 +51,15 @@ def test_baselines_stop_at_the_step_count():
     assert b["sample"].startswith("3 full oracle steps") and b["kind"] == "oracle" and b["value"] > 0
     b1 = bench.cpu_baseline_1thread(a)
     assert b1["cores"] == 1 and b1["sample"].startswith("3 full oracle steps") and b1["value"] > 0
+
+
+def test_reference_arm_line():
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "c1",
+                        "--steps", "2"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
