@@ -297,7 +297,8 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
 
 // ---- big i, small j: the fine cells within 2 h_i of i ---------------------
 // (rows pass by value through the out-of-line walks, so that the caller's
-// row stays in registers)
+// row stays in registers).  Cells are pruned as in walk_small, against their
+// tight boxes, and candidates are tested kGroup at a time.
 template <class S>
 __device__ __noinline__ S walk_big_fine(const NbArgs& a, const PatchDev* P, int64_t i, S row)
 {
@@ -313,6 +314,7 @@ __device__ __noinline__ S walk_big_fine(const NbArgs& a, const PatchDev* P, int6
     const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
     const float Rg = fmaxf(hf, P->hs_f) * Rc + slack;
     const float Rg2 = Rg * Rg;
+    const float qs = s_f * (1.0f / kBoxQ), qsz = sz_f * (1.0f / kBoxQ);
     const int Kb = min((int)ceilf(Rg / s_f), kMaxCellsAxis);
     const int Kz = min((int)ceilf(Rg / sz_f), kMaxCellsAxis);
     // a z block longer than the period: every z cell once, minimum image in FP32
@@ -323,11 +325,16 @@ __device__ __noinline__ S walk_big_fine(const NbArgs& a, const PatchDev* P, int6
     for (int iz = 0; iz < nz; iz++) {
         int czj, dcz;
         float gz2 = 0.0f;
+        // raw distance from i to the near z face of the plane (-big: every z
+        // cell visited, or the own plane)
+        float gzr = -1e30f;
+        uint32_t zshift = 20;
         if (!zw) {
             dcz = iz - Kz;
             czj = ((cz + dcz) % ncz + ncz) % ncz;
-            const float g = dcz > 0 ? (float)dcz * sz_f - ri.z : (dcz < 0 ? ri.z - (float)(dcz + 1) * sz_f : 0.0f);
-            const float gg = fmaxf(g, 0.0f);
+            if (dcz != 0) gzr = dcz > 0 ? (float)dcz * sz_f - ri.z : ri.z - (float)(dcz + 1) * sz_f;
+            zshift = dcz > 0 ? 20u : 25u;
+            const float gg = fmaxf(gzr, 0.0f);
             gz2 = gg * gg;
             if (gz2 >= Rg2) continue;
         } else {
@@ -339,35 +346,55 @@ __device__ __noinline__ S walk_big_fine(const NbArgs& a, const PatchDev* P, int6
         for (int dcy = -Kb; dcy <= Kb; dcy++) {
             const int cyj = cy + dcy;
             if ((unsigned)cyj >= (unsigned)ncy) continue;
-            const float g = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : 0.0f);
-            const float gy = fmaxf(g, 0.0f);
+            const float gyr = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : -1e30f);
+            const uint32_t yshift = dcy > 0 ? 10u : 15u;
+            const float gy = fmaxf(gyr, 0.0f);
             const float gzy2 = fmaf(gy, gy, gz2);
             if (gzy2 >= Rg2) continue;
             const float yo = ri.y - (float)dcy * s_f;
             const uint32_t lrow = cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx;
+#pragma unroll 1
             for (int dcx = -Kb; dcx <= Kb; dcx++) {
                 const int cxj = cx + dcx;
                 if ((unsigned)cxj >= (unsigned)ncx) continue;
-                const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : 0.0f);
+                const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : -1e30f);
                 const float gx = fmaxf(gxr, 0.0f);
                 const float d2 = fmaf(gx, gx, gzy2);
                 if (d2 >= Rg2) continue;
-                const uint32_t lin = lrow + (uint32_t)cxj;
-                const uint4 cr = a.g.cell[lin];
+                const uint4 cr = a.g.cell[lrow + (uint32_t)cxj];
                 const uint2 se = make_uint2(cr.x, cr.y);
                 if (se.x >= se.y) continue;
+                const float R = fmaxf(hf, __uint_as_float(cr.z)) * Rc + slack;
+                if (tight_gap2(cr.w, gxr, dcx > 0 ? 0u : 5u, gyr, yshift, gzr, zshift, qs, qsz) >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
                 const uint32_t kk = stencil_code(P, dcx, dcy, dcz, !zw) << kColBits;
-                for (uint32_t j = se.x; j < se.y; j++) {
-                    const float4 q = a.r4[j];
-                    const float dx = xo - q.x, dy = yo - q.y;
-                    float dz = zo - q.z;
-                    if (zw) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float T = fmaxf(Ti, q.w);
-                    if (r2 > T * fhi) continue;
+                // kGroup candidates at a time (the record array is padded past
+                // its end; slots past the cell are masked)
+                for (uint32_t jb = se.x; jb < se.y; jb += kGroup) {
+                    const float4* qp = a.r4 + jb;
+                    float4 q[kGroup];
+#pragma unroll
+                    for (int u = 0; u < kGroup; u++) q[u] = qp[u];
+                    const uint32_t rem = se.y - jb;
+                    float r2[kGroup], T[kGroup];
+                    unsigned near = 0;
+#pragma unroll
+                    for (int u = 0; u < kGroup; u++) {
+                        const float dx = xo - q[u].x, dy = yo - q[u].y;
+                        float dz = zo - q[u].z;
+                        if (zw) dz = fmaf(-lz_f, rintf(dz * inv_lz), dz);
+                        r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        T[u] = fmaxf(Ti, q[u].w);
+                        if ((uint32_t)u < rem && r2[u] <= T[u] * fhi) near |= 1u << u;
+                    }
+                    if (!near) continue;
                     const uint32_t c0 = row.mark();
-                    row.decide(a, P, i, j, r2, Ti, T, flo, fhi, j | kk);
+#pragma unroll
+                    for (int u = 0; u < kGroup; u++) {
+                        if (!(near & (1u << u))) continue;
+                        const uint32_t j = jb + (uint32_t)u;
+                        row.decide(a, P, i, j, r2[u], Ti, T[u], flo, fhi, j | kk);
+                    }
                     row.group_end(c0);
                 }
             }
