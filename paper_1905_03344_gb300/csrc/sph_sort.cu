@@ -280,7 +280,12 @@ __global__ void __launch_bounds__(256) k_keys(int64_t n, State s, const uint16_t
         const int p = patch_of[i];
         PatchDev* P = pd + p;
         const bool big = s.h[i] > P->hs;
-        if (big) atomicAdd(&P->nbig, 1);
+        // one atomic per warp and patch: the lanes of a warp that share the
+        // patch add their big particles together
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, p);
+        const unsigned bigs = __ballot_sync(act, big) & peers;
+        if (bigs && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P->nbig, __popc(bigs));
         const float tx = (float)(s.x[i] - P->xmin) * P->inv_s_f;
         const float ty = (float)(s.y[i] - P->ymin) * P->inv_s_f;
         const float tz = (float)(s.z[i] + 0.5 * P->lz) * P->inv_sz_f;
