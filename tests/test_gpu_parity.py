@@ -371,3 +371,31 @@ def test_batched_patches_match_single(B, orc):
         c = sim.conserved(p)
         assert c[0] == pytest.approx(r.conserved()[0], rel=1e-14)
     sim.close()
+
+
+@pytest.mark.parametrize("precision,tol_p,tol_l", [("fp64", 1e-12, 1e-12), ("mixed", 2e-5, 1e-7)])
+def test_long_run_momentum_and_lz(B, precision, tol_p, tol_l, report):
+    """200 steps of the 40^3 patch on the GPU alone: every pair force is
+    central and enters both particles with opposite signs, so the total
+    momentum (zero by the lattice's symmetry) and L_z stay at their initial
+    values to rounding through the leapfrog (A12's definitions).  In FP64
+    that rounding is ~1e-16.  The mixed path sums each side of a pair in
+    FP32 in its own particle's row, so a particle's force carries a rounding
+    of order eps32 sum_j |F_ij| that the other side does not mirror; with the
+    pressure offset the pair terms are ~10x the net force, and the total
+    momentum drifts at ~6e-6 of sum m |v| over the run (measured), while L_z,
+    a sum of x * F over the same terms, keeps ~4e-9."""
+    f = inputs.square_patch(40)
+    sim = B.SPH(len(f["x"]), precision=precision)
+    sim.set_particles(f)
+    sim.step(1)
+    c0 = sim.conserved()
+    scale = float(np.sum(f["m"] * np.hypot(f["vx"], f["vy"])))
+    sim.step(199)
+    c = sim.conserved()
+    sim.close()
+    dp = max(abs(c[1]), abs(c[2]), abs(c[3])) / scale
+    dl = abs(c[4] - c0[4]) / abs(c0[4])
+    report["long200/%s" % precision] = dict(momentum=dp, lz=dl, p=[float(v) / scale for v in c[1:4]])
+    assert c[0] == pytest.approx(c0[0], rel=1e-14)
+    assert dp <= tol_p and dl <= tol_l, (dp, dl)
