@@ -379,12 +379,14 @@ def test_long_run_momentum_and_lz(B, precision, tol_p, tol_l, report):
     central and enters both particles with opposite signs, so the total
     momentum (zero by the lattice's symmetry) and L_z stay at their initial
     values to rounding through the leapfrog (A12's definitions).  In FP64
-    that rounding is ~1e-16.  The mixed path sums each side of a pair in
-    FP32 in its own particle's row, so a particle's force carries a rounding
-    of order eps32 sum_j |F_ij| that the other side does not mirror; with the
-    pressure offset the pair terms are ~10x the net force, and the total
-    momentum drifts at ~6e-6 of sum m |v| over the run (measured), while L_z,
-    a sum of x * F over the same terms, keeps ~4e-9."""
+    that rounding is ~1e-16.  The mixed path evaluates each pair term exactly
+    antisymmetrically but sums each particle's row in FP32 (four terms
+    plainly, then a Kahan step), and along the periodic, gradient-free z axis
+    of the lattice every particle sums nearly the same cancelling terms in
+    the same order: the rounding is the same for all of them and adds up to a
+    uniform z force instead of averaging out.  P_z drifts by ~6e-6 of
+    sum m |v| over the run (P_x, P_y ~1e-9, measured), while L_z, untouched
+    by a uniform force about the centroid, keeps ~4e-9."""
     f = inputs.square_patch(40)
     sim = B.SPH(len(f["x"]), precision=precision)
     sim.set_particles(f)
