@@ -63,3 +63,14 @@ def test_create_without_gpu_fails_cleanly(lib):
     with pytest.raises(binding.SphError) as e:
         binding.sph_create()
     assert e.value.status == binding.SPH_ECUDA
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library every call path raises."""
+    from paper_1905_03344_gb300 import binding
+    monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "libsph_gb300.so"))
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(ImportError):
+        binding.lib()
+    with pytest.raises(ImportError):
+        binding.SPH(8)
