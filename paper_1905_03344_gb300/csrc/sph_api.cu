@@ -1312,7 +1312,7 @@ sph_status sph_autotune(sph_ctx* ctx)
     ctx->prof = false;
     destroy_graphs(ctx);
     const double factors[4] = {1.0 / 3.0, 0.5, 0.75, 1.0};
-    const int pair_tpps[4] = {4, 8, 16, 32};
+    const int pair_tpps[6] = {1, 2, 4, 8, 16, 32};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -158,7 +158,7 @@ def test_fp64_pair_sums(B, orc, case, report):
 
 
 @pytest.mark.parametrize("case", sorted(FORCE_CASES))
-@pytest.mark.parametrize("tpp", [4, 8, 32])
+@pytest.mark.parametrize("tpp", [1, 2, 4, 8, 32])
 def test_mixed_pair_sums(B, orc, case, tpp, report):
     f = FORCE_CASES[case]()
     lz = f.pop("lz", 1.0)
