@@ -60,9 +60,11 @@ NB_BYTES_PER_PARTICLE = 48
 # dram__bytes_write.sum divided by the launch's 1.024e8 list entries;
 # profiles/k_nb_thread_square_patch_100cubed.md and
 # profiles/k_momentum_mixed_square_patch_100cubed.md), scaled to the
-# benchmark's launch by its entries.  None once the kernel has changed since.
+# benchmark's launch by its entries.  None once the kernel has changed since;
+# the momentum figure is that of its 2-lanes-per-particle instantiation.
 NB_DRAM_BYTES_PER_ENTRY = 5.91
-MOMENTUM_DRAM_BYTES_PER_ENTRY = 6.59
+MOMENTUM_DRAM_BYTES_PER_ENTRY = 6.61
+MOMENTUM_DRAM_TPP = 2
 
 WORKLOADS = {
     "c1": ("square patch 20^3 (8,000 particles), omega=5", 20),
@@ -426,7 +428,7 @@ def main():
                 # the DRAM figure is the standard Wendland variant's
                 "traffic": (MOMENTUM_DRAM_BYTES_PER_ENTRY * pairs_per_step)
                 if MOMENTUM_DRAM_BYTES_PER_ENTRY and args.kernel == "wendland" and not args.grad_h
-                and mode == "lists" and args.precision == "mixed" else None,
+                and mode == "lists" and args.precision == "mixed" and tpp == MOMENTUM_DRAM_TPP else None,
                 "peak_source": pair_peak_src,
                 "peak_fma_measured": fma_peak, "frac_of_fma_measured": mom_tf and mom_tf / fma_peak,
                 "flops_per_pair": flops_pair, "ms_per_launch": mom_ms,
