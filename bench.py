@@ -32,8 +32,9 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # FP32 operations per pair (FMA = 2, MUFU and min/max not counted), counted by
-# hand from k_momentum_mixed and k_density_mixed (the per-line count is in the
-# design notes)
+# hand from k_momentum_mixed and k_density_mixed.  Momentum: separation 9, r^2 5,
+# r 2, q_i 2, w_j^2 and w_j q_j 3, F 7, v_ij 3, v.r 5, h sum 1, mu 6, Pi 7, g 1,
+# (A_i + A_j + Pi) g 3, force terms 3, du term 5, sums 8 = 70
 FLOPS_PER_PAIR_MOMENTUM = 70
 FLOPS_PER_PAIR_DENSITY = 28
 # the Sinc kernel (n = 6) in k_momentum_mixed: the Wendland count with its

@@ -140,7 +140,9 @@ typedef struct {
 /* Fills the defaults listed above (max_particles = 1<<20, max_patches = 1). */
 void sph_config_default(sph_config* cfg);
 
-/* Creates a context and allocates all device memory for the capacities in
+/* One instance of the solver library the paper describes (its parts are
+ * independent libraries callable from other codes, Sec. 1).
+ * Creates a context and allocates all device memory for the capacities in
  * cfg.  Errors: SPH_EINVAL (bad cfg), SPH_ENOMEM, SPH_ECUDA (no device). */
 sph_status sph_create(const sph_config* cfg, sph_ctx** out);
 
@@ -153,15 +155,21 @@ const char* sph_status_string(sph_status s);
 
 /* Sets n particles (0 <= n <= max_particles); arrays of n doubles each, in the
  * caller's order: position, velocity (v_{-1/2} := v_0), mass, smoothing
- * length, specific internal energy.  Resets the time state (step 0,
- * dt_{-1} = 0, du_{-1} = 0, a_{-1} = 0) and makes all particles one patch.
+ * length, specific internal energy.  These are the particle fields of the
+ * square-patch test of Sec. 4 (lattice positions in a periodic-z box, the
+ * rotation velocity of Eq. 3, the internal energy of the series pressure);
+ * any other particle set is accepted the same way.  Resets the time state
+ * (step 0, dt_{-1} = 0, du_{-1} = 0, a_{-1} = 0) and makes all particles one
+ * patch.  The arrays are copied; the caller keeps them.
  * Errors: SPH_EINVAL (n out of range, NULL pointer), SPH_ECUDA. */
 sph_status sph_set_particles(sph_ctx* ctx, int64_t n, const double* x, const double* y,
                              const double* z, const double* vx, const double* vy,
                              const double* vz, const double* m, const double* h,
                              const double* u, int on_device);
 
-/* Splits the particles into independent patches: patch p is particles
+/* The paper has no counterpart: it runs one patch per job.  This call
+ * batches many independent problems into one launch per phase.
+ * Splits the particles into independent patches: patch p is particles
  * [offsets[p], offsets[p+1]) of the original order, offsets[0] = 0,
  * offsets[n_patches] = n.  Each patch has its own grid, time-step and
  * conserved sums, and its own z period lz.  Valid only right after
@@ -210,7 +218,10 @@ sph_status sph_density(sph_ctx* ctx);
  * v_{n-1/2} + a_{n-1} dt_{n-1}/2.  Errors: SPH_ESTATE (no density). */
 sph_status sph_momentum_energy(sph_ctx* ctx);
 
-/* nsteps full timesteps: neighbours, density + EOS, momentum + energy,
+/* nsteps full timesteps of the mini-app's solver (Sec. 3): the Courant
+ * condition on a global time-step (Table 1 "Global"), positions by the Press
+ * (leapfrog) method and the energy by Adams-Bashforth.  Each step runs
+ * neighbours, density + EOS, momentum + energy,
  * Courant dt_n = min(C min h/c, dt_growth dt_{n-1}) per patch, kick
  * v_{n+1/2} = v_{n-1/2} + a_n (dt_n + dt_{n-1})/2, drift x += v_{n+1/2} dt_n
  * (z wrapped), Adams-Bashforth energy, h adaptation, conserved sums.
@@ -218,7 +229,9 @@ sph_status sph_momentum_energy(sph_ctx* ctx);
  * Errors: SPH_EOVERFLOW, SPH_ENONFINITE, SPH_ETIMEOUT, SPH_ESTATE. */
 sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last);
 
-/* Conserved sums of patch (or all patches for patch = -1) from the current
+/* The quantities whose conservation the square-patch test of Sec. 4 is used
+ * to check (Sec. 4 stresses enforcing the fundamental conservation laws).
+ * Conserved sums of patch (or all patches for patch = -1) from the current
  * state, out (host) = { M, Px, Py, Pz, Lz, Ekin, Eint }: M = sum m,
  * P = sum m v, Lz = sum m (x v_y - y v_x), Ekin = sum m v^2/2, Eint = sum m u,
  * computed in FP64 with a deterministic two-level reduction. */
@@ -230,14 +243,18 @@ sph_status sph_get_field(sph_ctx* ctx, int32_t field, double* dst, int on_device
 /* Time state of a patch: last dt, the dt used as dt_{n-1}, steps taken. */
 sph_status sph_get_dt(sph_ctx* ctx, int32_t patch, double* dt, double* dt_prev, int64_t* step);
 
-/* Checkpoint: with buf = NULL, *bytes receives the size needed; otherwise the
+/* The mini-app has no checkpoint/restart (Table 2); the paper lists
+ * checkpointing as future work (Sec. 5).  Here it is a state save/restore.
+ * Checkpoint: with buf = NULL, *bytes receives the size needed; otherwise the
  * full time state (particle fields in internal order, permutation, patch
  * table, dt state) is written to the host buffer buf.  sph_set_state restores
  * it; stepping then continues bit for bit as without the checkpoint. */
 sph_status sph_get_state(sph_ctx* ctx, void* buf, size_t* bytes);
 sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes);
 
-/* Times the neighbour and pair-sum phases for a few candidate launch
+/* The paper has no counterpart (it tunes nothing at run time): a launch-shape
+ * autotuner of this library.
+ * Times the neighbour and pair-sum phases for a few candidate launch
  * configurations (threads per particle, cell factor and, with
  * SPH_PAIRS_AUTO, lists against the list-free sums) on the current
  * particles and keeps the fastest; the particle state is left unchanged. */
@@ -305,7 +322,10 @@ sph_status sph_get_pair_count(sph_ctx* ctx, int64_t* total, int reset);
  * device memory (256 KB, kept by every GPU that loads the library until the
  * process exits), so n is limited to 16,777,216; larger n returns
  * SPH_EINVAL.  The first call on a device looks up the array's device
- * address (do that first call before any stream capture).  Every call
+ * address (do that first call before any stream capture) and keeps it for
+ * the life of the process: after cudaDeviceReset, or anything else that
+ * replaces the device's primary context, the kept address is stale and this
+ * entry point must not be called again on that device.  Every call
  * overwrites the array: calls whose work overlaps on the GPU race.
  * Errors: SPH_EINVAL (n out of range, NULL pointer), SPH_ECUDA;
  * sph_noalloc_last_error() gives the message. */

@@ -26,7 +26,8 @@ _REPORT = {}
 def report():
     """Measured parity errors; merged into the JSON file named by the
     environment variable SPH_PARITY_REPORT (when set) at the end of the
-    session, for the design notes."""
+    session: the measured margins of every parity test, kept to compare
+    runs and to set tolerances from."""
     return _REPORT
 
 
