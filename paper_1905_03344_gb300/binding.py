@@ -327,17 +327,47 @@ def sph_get_pair_count(ctx, reset=False):
     return v.value
 
 
-def sph_conserved_noalloc(fields, out, stream=None):
-    """Conserved sums of device arrays without any allocation: fields holds
-    x y vx vy vz m u as float64 CUDA tensors of equal length, out is a
-    float64 CUDA tensor of 7 elements; asynchronous on stream (a CUDA stream
-    handle or None)."""
+def _noalloc_args(fields, out):
+    """Checks the arguments of sph_conserved_noalloc without touching the
+    device: seven float64 fields of one length n, a float64 out of at least 7
+    elements, all contiguous CUDA tensors on the current device.  Returns the
+    field tensors in the C ABI's order and n."""
     names = ["x", "y", "vx", "vy", "vz", "m", "u"]
+    missing = [k for k in names if k not in fields]
+    if missing:
+        raise ValueError("sph_conserved_noalloc: missing fields %s" % missing)
     arrs = [fields[k] for k in names]
-    n = len(arrs[0])
-    for a in arrs + [out]:
-        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
-            raise ValueError("sph_conserved_noalloc takes contiguous CUDA tensors")
+    import torch
+    for k, a in zip(names + ["out"], arrs + [out]):
+        if not isinstance(a, torch.Tensor):
+            raise ValueError("sph_conserved_noalloc: %s must be a torch tensor" % k)
+        if a.dtype != torch.float64:
+            raise ValueError("sph_conserved_noalloc: %s must be float64, not %s" % (k, a.dtype))
+    n = arrs[0].numel()
+    for k, a in zip(names, arrs):
+        if a.numel() != n:
+            raise ValueError("sph_conserved_noalloc: %s has %d elements, x has %d" % (k, a.numel(), n))
+    if out.numel() < 7:
+        raise ValueError("sph_conserved_noalloc: out must hold 7 elements, it has %d" % out.numel())
+    for k, a in zip(names + ["out"], arrs + [out]):
+        if not (a.is_cuda and a.is_contiguous()):
+            raise ValueError("sph_conserved_noalloc: %s must be a contiguous CUDA tensor" % k)
+    dev = torch.cuda.current_device()
+    for k, a in zip(names + ["out"], arrs + [out]):
+        if a.device.index != dev:
+            raise ValueError("sph_conserved_noalloc: %s is on cuda:%d, the current device is cuda:%d"
+                             % (k, a.device.index, dev))
+    return arrs, n
+
+
+def sph_conserved_noalloc(fields, out, stream=None):
+    """Conserved sums (M, Px, Py, Pz, Lz, Ekin, Eint) of device arrays without
+    any allocation: fields holds x y vx vy vz m u as float64 CUDA tensors of
+    equal length on the current device, out is a float64 CUDA tensor of at
+    least 7 elements; asynchronous on stream (a CUDA stream handle or None).
+    Calls whose kernels overlap on the GPU race on the library's one scratch
+    array."""
+    arrs, n = _noalloc_args(fields, out)
     st = lib().sph_conserved_noalloc(n, *[ctypes.c_void_p(a.data_ptr()) for a in arrs],
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
     if st != SPH_OK:

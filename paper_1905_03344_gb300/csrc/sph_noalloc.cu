@@ -11,7 +11,10 @@
 // name as a device address; its address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
 // that device, and passed to the kernels.  That first call should therefore
-// come before any stream capture.  All calls share the one array: it is
+// come before any stream capture.  The address is kept for the life of the
+// process: a device reset (cudaDeviceReset, or a new primary context on that
+// device) makes it stale, and the entry point must not be called on that
+// device afterwards.  All calls share the one array: it is
 // overwritten by every call (each block writes its own slot before the final
 // sum reads it, so nothing needs clearing), and calls whose kernels overlap on
 // the GPU race on it.

@@ -2,15 +2,18 @@
 for callers that cannot call cudaMalloc (work recorded into a CUDA graph, host
 frameworks that own the allocator).  Its scratch is a fixed array inside the
 library.  Checked through the C ABI against sph_conserved, the entry point
-that uses the context's allocated scratch, on two calls in a row (the second
-call finds the array holding the first call's values).  This file is named to
-be collected last."""
+that uses the context's allocated scratch, and against the oracle's sums, on
+calls in a row whose sizes shrink: a later call finds the array holding the
+slots of a larger earlier call, which it must not read.  This file is named
+to be collected last."""
 import numpy as np
 import pytest
 
 from paper_1905_03344_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+NAMES = ("x", "y", "vx", "vy", "vz", "m", "u")
 
 
 @pytest.fixture(scope="module")
@@ -23,31 +26,57 @@ def B():
     return binding
 
 
-def _fields(seed):
-    f = inputs.random_cloud(20000, seed=seed, vscale=2.0)
+def _fields(n, seed):
+    f = inputs.random_cloud(n, seed=seed, vscale=2.0)
     f["x"] = f["x"] + 0.25     # nonzero angular momentum and linear momentum
     return f
 
 
-def test_noalloc_matches_allocating_entry_point(B):
+def _scales(f):
+    """Per sum, the sum of its terms' magnitudes: the scale of its rounding."""
+    m = f["m"]
+    return np.array([m.sum(), (m * np.abs(f["vx"])).sum(), (m * np.abs(f["vy"])).sum(),
+                     (m * np.abs(f["vz"])).sum(),
+                     (m * (np.abs(f["x"] * f["vy"]) + np.abs(f["y"] * f["vx"]))).sum(),
+                     (0.5 * m * (f["vx"] ** 2 + f["vy"] ** 2 + f["vz"] ** 2)).sum(),
+                     (m * np.abs(f["u"])).sum()])
+
+
+def _noalloc(B, f):
     import torch
-    for call, seed in enumerate((0, 1)):
-        f = _fields(seed)
-        n = len(f["x"])
+    dev = {k: torch.tensor(f[k], dtype=torch.float64, device="cuda") for k in NAMES}
+    out = torch.full((7,), np.nan, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    B.sph_conserved_noalloc(dev, out, stream.cuda_stream)
+    stream.synchronize()
+    return out.cpu().numpy()
+
+
+def test_noalloc_matches_allocating_entry_point_and_oracle(B, orc):
+    # 60000 particles fill 15 scratch slots; the calls after it use 5 and 2
+    for call, (n, seed) in enumerate(((60000, 0), (20000, 1), (5000, 2))):
+        f = _fields(n, seed)
         sim = B.SPH(n, precision="fp64")
         sim.set_particles(f)
         ref = sim.conserved()
         sim.close()
-        dev = {k: torch.tensor(f[k], dtype=torch.float64, device="cuda") for k in
-               ("x", "y", "vx", "vy", "vz", "m", "u")}
-        out = torch.full((7,), np.nan, dtype=torch.float64, device="cuda")
-        stream = torch.cuda.current_stream()
-        B.sph_conserved_noalloc(dev, out, stream.cuda_stream)
-        stream.synchronize()
-        got = out.cpu().numpy()
-        scale = np.abs(ref).max()
+        got = _noalloc(B, f)
+        want = orc.conserved(*[f[k] for k in NAMES])
+        tol = 1e-12 * _scales(f)
         assert np.all(np.isfinite(got)), call
-        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * scale), (call, got, ref)
+        assert np.all(np.abs(got - ref) <= tol), (call, got, ref)
+        assert np.all(np.abs(got - want) <= tol), (call, got, want)
+
+
+def test_noalloc_of_no_particles_is_zero(B):
+    import torch
+    # after a call that filled slots, n = 0 reads none of them
+    _noalloc(B, _fields(30000, 3))
+    dev = {k: torch.zeros(0, dtype=torch.float64, device="cuda") for k in NAMES}
+    out = torch.full((7,), np.nan, dtype=torch.float64, device="cuda")
+    B.sph_conserved_noalloc(dev, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.current_stream().synchronize()
+    assert np.all(out.cpu().numpy() == 0.0)
 
 
 def test_noalloc_rejects_beyond_its_fixed_scratch(B):
