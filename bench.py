@@ -250,7 +250,8 @@ def main():
     ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="steps of the end-to-end leg (-1: as many as the timed steps; 0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel", default="wendland", choices=["wendland", "sinc"],
@@ -333,6 +334,12 @@ def main():
     tpp_den = binding.sph_get_density_tpp(sim.ctx)
     mode = sim.pair_mode()
     torch.cuda.synchronize()
+    # the state at the start of the timed steps, on the host: the end-to-end
+    # leg below runs the same steps from it
+    e2e_blob = None
+    if args.e2e_steps != 0:
+        e2e_blob = torch.empty(sim.state_bytes(), dtype=torch.uint8).pin_memory()
+        sim.get_state(e2e_blob)
     sim.pair_count(reset=True)
     # the timed region runs the phases with CUDA events between them (per-kernel
     # durations for the roofline); the graph is bypassed while profiling
@@ -534,24 +541,32 @@ def main():
         if not args.no_autotune:
             sim.autotune()
 
-    # end to end through the C ABI with host (pinned) buffers
-    if args.e2e_steps > 0:
-        hfields = {k: torch.tensor(v, dtype=torch.float64).pin_memory() for k, v in f.items()}
+    # end to end through the C ABI with host (pinned) buffers: every step
+    # uploads the whole time state from host memory (sph_set_state: fields,
+    # permutation, dt state), takes one step and reads the whole new state
+    # back (sph_get_state), which the next step uploads.  Starting from the
+    # state saved at the start of the timed region, these are the same steps
+    # as the timed ones (all K of them by default).
+    if e2e_blob is not None:
+        ne2e = args.steps if args.e2e_steps < 0 else args.e2e_steps
+        nbytes = e2e_blob.numel()
+        sim.set_state(e2e_blob)
+        sim.step(1)                 # untimed: the launch shape's graph and rows for this order
+        sim.set_state(e2e_blob)
         sim.pair_count(reset=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            sim.set_particles(hfields)
-            if offsets is not None:
-                sim.set_patches(offsets)
+        for _ in range(ne2e):
+            sim.set_state(e2e_blob)
             sim.step(1)
-            sim.conserved()
+            sim.get_state(e2e_blob)
         el = time.perf_counter() - t0
         pe = sim.pair_count(reset=True)
-        line["e2e"] = {"value": 2.0 * pe / el, "unit": UNIT, "h2d_bytes_per_step": 9 * 8 * n,
-                       "d2h_bytes_per_step": 7 * 8 + 8, "steps": args.e2e_steps,
-                       "ms_per_step": 1e3 * el / args.e2e_steps,
-                       "call": "sph_set_particles(host) + sph_step(1) + sph_conserved per step"}
+        line["e2e"] = {"value": 2.0 * pe / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "steps": ne2e, "ms_per_step": 1e3 * el / ne2e,
+                       "call": "per step: sph_set_state(pinned host state) + sph_step(1) + "
+                               "sph_get_state(pinned host state): all 13 particle fields, the "
+                               "permutation and the dt state in and out; the timed region's steps"}
     sim.close()
 
     # the oracle baseline is of the square patch (c1-c3)

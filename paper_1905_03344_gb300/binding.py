@@ -259,17 +259,49 @@ def sph_get_dt(ctx, patch=0):
     return dt.value, dtp.value, step.value
 
 
-def sph_get_state(ctx):
+def sph_state_bytes(ctx):
+    """Size of the checkpoint of the current state."""
     nb = ctypes.c_size_t()
     _check(ctx, lib().sph_get_state(ctx, None, ctypes.byref(nb)))
+    return nb.value
+
+
+def _host_buffer(buf):
+    """(pointer, size in bytes) of a host uint8 buffer: a CPU torch tensor
+    (pinned memory makes the copies fast) or a numpy array."""
+    if hasattr(buf, "data_ptr"):
+        if buf.is_cuda or not buf.is_contiguous():
+            raise ValueError("state buffer: a contiguous host tensor")
+        return ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()
+    if not buf.flags["C_CONTIGUOUS"]:
+        raise ValueError("state buffer: a contiguous array")
+    return ctypes.c_void_p(buf.ctypes.data), buf.nbytes
+
+
+def sph_get_state(ctx, out=None):
+    """The checkpoint as bytes, or, with out (a host uint8 tensor or array of
+    at least sph_state_bytes(ctx) bytes), written into out; returns its size
+    then."""
+    if out is not None:
+        p, size = _host_buffer(out)
+        nb = ctypes.c_size_t(size)
+        _check(ctx, lib().sph_get_state(ctx, p, ctypes.byref(nb)))
+        return nb.value
+    nb = ctypes.c_size_t(sph_state_bytes(ctx))
     buf = ctypes.create_string_buffer(nb.value)
     _check(ctx, lib().sph_get_state(ctx, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(nb)))
     return buf.raw[: nb.value]
 
 
-def sph_set_state(ctx, blob):
-    buf = ctypes.create_string_buffer(blob, len(blob))
-    _check(ctx, lib().sph_set_state(ctx, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+def sph_set_state(ctx, blob, nbytes=None):
+    """Restores a checkpoint: bytes, or a host uint8 tensor or array holding
+    nbytes (default: all of it) of one."""
+    if isinstance(blob, (bytes, bytearray)):
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(ctx, lib().sph_set_state(ctx, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+        return
+    p, size = _host_buffer(blob)
+    _check(ctx, lib().sph_set_state(ctx, p, size if nbytes is None else int(nbytes)))
 
 
 def sph_autotune(ctx):
@@ -456,13 +488,22 @@ class SPH:
     def dt(self, patch=0):
         return sph_get_dt(self.ctx, patch)
 
-    def get_state(self):
-        return sph_get_state(self.ctx)
+    def get_state(self, out=None):
+        return sph_get_state(self.ctx, out)
 
-    def set_state(self, blob):
-        sph_set_state(self.ctx, blob)
+    def state_bytes(self):
+        return sph_state_bytes(self.ctx)
+
+    def set_state(self, blob, nbytes=None):
+        sph_set_state(self.ctx, blob, nbytes)
         import struct
-        self.n = struct.unpack_from("<q", blob, 16)[0]
+        if isinstance(blob, (bytes, bytearray)):
+            head = bytes(blob[:24])
+        elif hasattr(blob, "numpy"):
+            head = blob[:24].numpy().tobytes()
+        else:
+            head = blob[:24].tobytes()
+        self.n = struct.unpack_from("<q", head, 16)[0]
 
     def autotune(self):
         sph_autotune(self.ctx)

@@ -51,6 +51,16 @@ __global__ void k_scatter_u32(int64_t n, const uint32_t* src, const uint32_t* pe
         dst[perm[k]] = src[k];
 }
 
+// dst[k] = src[perm[k]]: a caller's-order array into a sorted order; a
+// permutation entry out of range (a damaged state buffer) gives 0
+__global__ void k_gather_u32(int64_t n, const uint32_t* src, const uint32_t* perm, uint32_t* dst)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[k];
+        dst[k] = (int64_t)j < n ? src[j] : 0u;
+    }
+}
+
 __global__ void k_accum_pairs(const unsigned long long* total, unsigned long long* acc, const int* status)
 {
     if (!(*status & kStBad)) *acc += *total;
@@ -1278,6 +1288,14 @@ sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes)
     std::vector<double> times(3 * np);
     memcpy(times.data(), p, sizeof(double) * 3 * np);
     p += sizeof(double) * 3 * np;
+    // as in sph_set_particles: the last lists' row lengths, carried to the
+    // caller's order and then into the restored state's order, reserve the
+    // rows of its first search (a state saved by this context a step ago
+    // gets its own rows back; any other hint is only a poorer guess)
+    const bool carry = ctx->cnt_valid && n == ctx->n && n > 0;
+    const int cgrid = (int)((n + 255) / 256 < ctx->sms * 16 ? (n + 255) / 256 : ctx->sms * 16);
+    if (carry) k_scatter_u32<<<cgrid, 256, 0, ctx->stream>>>(n, ctx->cnt, ctx->perm[ctx->cur], ctx->cnt_orig);
+    CK(cudaStreamSynchronize(ctx->stream));
     ctx->cur = 0;
     ctx->n = n;
     if (n > 0) {
@@ -1298,6 +1316,13 @@ sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes)
         pd[q].step = (int64_t)times[3 * q + 2];
     }
     CK(cudaMemcpy(ctx->pd, pd.data(), sizeof(PatchDev) * np, cudaMemcpyHostToDevice));
+    if (carry) {
+        k_gather_u32<<<cgrid, 256, 0, ctx->stream>>>(n, ctx->cnt_orig, ctx->perm[0], ctx->cnt);
+        CK(cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream));
+        ctx->cnt_valid = true;
+        st = after_launches(ctx, "sph_set_state");
+        if (st != SPH_OK) return st;
+    }
     ctx->fresh = true;
     ctx->nnz = -1;
     return SPH_OK;

@@ -1,5 +1,5 @@
-// sph_fused.cuh -- the list-free pair sums: the density (A5 + A6) and the
-// momentum and energy sums (A7) evaluated inside the neighbour search, with
+// sph_fused.cuh -- the list-free pair sums: the density (with the EOS) and
+// the momentum and energy sums evaluated inside the neighbour search, with
 // no neighbour lists in memory.
 //
 // Each kernel walks the candidates of every particle exactly as the list

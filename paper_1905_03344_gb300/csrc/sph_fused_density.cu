@@ -1,5 +1,5 @@
-// sph_fused_density.cu -- the list-free density pass (A5 + A6 inside the
-// neighbour search, with |N(i)| and n_i), mixed precision and FP64; the
+// sph_fused_density.cu -- the list-free density pass (density and EOS inside
+// the neighbour search, with |N(i)| and n_i), mixed precision and FP64; the
 // kernels are in sph_fused.cuh.
 #include "sph_fused.cuh"
 

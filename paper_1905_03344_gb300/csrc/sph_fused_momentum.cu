@@ -1,5 +1,5 @@
-// sph_fused_momentum.cu -- the list-free momentum and energy pass (A7 inside
-// the neighbour search), mixed precision and FP64; the kernels are in
+// sph_fused_momentum.cu -- the list-free momentum and energy pass (the pair
+// sums inside the neighbour search), mixed precision and FP64; the kernels are in
 // sph_fused.cuh.
 #include "sph_fused.cuh"
 

@@ -59,7 +59,7 @@ __device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowA
 }
 
 // ---------------------------------------------------------------------------
-// A5 + A6, mixed precision
+// density + EOS, mixed precision
 // ---------------------------------------------------------------------------
 // the row of one particle: plain FP32 weights m_j W-shape(r), Kahan sum, four
 // neighbours per lane and iteration (their gathers are issued together)
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// A5 + A6, FP64
+// density + EOS, FP64
 // ---------------------------------------------------------------------------
 template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// A7, mixed precision
+// momentum + energy, mixed precision
 // ---------------------------------------------------------------------------
 // The row in chunks of four words: a lane loads its chunk with one 16-byte
 // load (rows start on 32-byte boundaries and are reserved in multiples of 8
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
 }
 
 // ---------------------------------------------------------------------------
-// A7, FP64
+// momentum + energy, FP64
 // ---------------------------------------------------------------------------
 template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)

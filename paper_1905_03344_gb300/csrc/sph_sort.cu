@@ -427,7 +427,7 @@ static int scan_u32(const Launch& L, int64_t n, const uint32_t* in, uint32_t* ou
 }
 
 // ---------------------------------------------------------------------------
-// A2: stable LSD radix sort, 8-bit digits.  Per pass: a digit histogram per
+// Stable LSD radix sort, 8-bit digits.  Per pass: a digit histogram per
 // tile of 4096 keys (digit-major), an exclusive scan of the histograms, and a
 // scatter that ranks keys stably inside the tile (warp match + per-warp
 // counters, warps in tile order), stages the tile in shared memory in digit
@@ -565,7 +565,7 @@ int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, ui
 }
 
 // ---------------------------------------------------------------------------
-// A2b/A3: gather every field into sorted order, write the permutation, the
+// Gather every field into sorted order, write the permutation, the
 // cell table (start/end by key boundaries, largest h per cell) and the FP32
 // records with positions relative to the particle's cell origin.  Also forms
 // the time-centred velocity v_{n-1/2} + a_{n-1} dt_{n-1}/2 used by the
@@ -701,7 +701,7 @@ int launch_refresh_records(const Launch& L, int64_t n, const State& s, const uin
 }
 
 // ---------------------------------------------------------------------------
-// A3': the tight box of each non-empty fine cell, from its particles' FP32
+// The tight box of each non-empty fine cell, from its particles' FP32
 // offsets, quantised outward to 1/kBoxQ of the cell edge (see Grid).  One
 // thread per cell; blockIdx.y is the patch.
 // ---------------------------------------------------------------------------

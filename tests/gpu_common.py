@@ -49,3 +49,27 @@ def scaled(g, o, scale):
 def zdist(a, b, lz=1.0):
     d = np.asarray(a) - np.asarray(b)
     return np.abs(d - lz * np.round(d / lz))
+
+
+CONSERVED = ("M", "Px", "Py", "Pz", "Lz", "Ekin", "Eint")
+
+
+def conserved_scales(x, y, vx, vy, vz, m, u):
+    """For each of the 7 conserved sums (M, P, L_z, E_kin, E_int), the sum of
+    its terms' magnitudes: the natural scale of its rounding error (P of the
+    square patch is zero by symmetry, so a relative error of P itself is
+    undefined).  The components of P share the scale sum m |v| (the vector's
+    magnitude, as for vector fields in the tolerance norm): v_z of the
+    z-periodic patch is itself rounding noise."""
+    x, y, vx, vy, vz, m, u = (np.asarray(a, dtype=np.float64) for a in (x, y, vx, vy, vz, m, u))
+    pv = (m * np.sqrt(vx * vx + vy * vy + vz * vz)).sum()
+    return np.array([m.sum(), pv, pv, pv,
+                     (m * (np.abs(x * vy) + np.abs(y * vx))).sum(),
+                     (0.5 * m * (vx * vx + vy * vy + vz * vz)).sum(), (m * np.abs(u)).sum()])
+
+
+def conserved_errors(g, o, scales):
+    """{name: |g - o| / scale} for the 7 conserved sums."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    return {k: float(abs(g[q] - o[q]) / max(scales[q], 1e-300)) for q, k in enumerate(CONSERVED)}

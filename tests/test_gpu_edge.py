@@ -171,6 +171,37 @@ def test_checkpoint_resume_bitwise(B, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_state_round_trip_every_step_bitwise(B, precision):
+    """The end-to-end use of the C ABI: each step uploads the whole state from
+    a pinned host buffer (sph_set_state, which carries the context's last row
+    lengths into the restored order as reservation hints), steps once and
+    reads the state back (sph_get_state).  Bit for bit the same as stepping on
+    the device; the first restore into a context that has stepped a different
+    state gets foreign hints, which only cost a repair."""
+    import torch
+    f = inputs.square_patch(14)
+    n = len(f["x"])
+    ref = B.SPH(n, precision=precision)
+    ref.set_particles(f)
+    ref.step(2)
+    buf = torch.empty(ref.state_bytes(), dtype=torch.uint8).pin_memory()
+    assert ref.get_state(buf) == buf.numel()
+    sim = B.SPH(n, precision=precision)
+    sim.set_particles(inputs.random_cloud(n, seed=3))     # other lists, other hints
+    sim.step(1)
+    for _ in range(4):
+        sim.set_state(buf)
+        sim.step(1)
+        sim.get_state(buf)
+        ref.step(1)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "du_prev", "nown", "nnb"):
+        assert np.array_equal(sim.field(k), ref.field(k)), k
+    assert sim.dt() == ref.dt()
+    sim.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_graph_replay_bitwise(B, precision):
     f = inputs.square_patch(12)
     n = len(f["x"])

@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 from paper_1905_03344_gb300 import inputs
-from gpu_common import normwise, normwise_vec, scaled
+from gpu_common import conserved_errors, conserved_scales, normwise, normwise_vec, scaled
 
 pytestmark = pytest.mark.gpu
 
@@ -141,7 +141,9 @@ def test_batched_64_patches(B, orc, report):
     s64.step(1)
     x, hh = s64.field("x"), s64.field("h")
     dts = [s64.dt(p)[0] for p in range(64)]
+    cons = [s64.conserved(p) for p in range(64)]
     s64.close()
+    worst_c = 0.0
     for p in range(64):
         a, b = int(offsets[p]), int(offsets[p + 1])
         ref = orc.Sim({k: v[a:b] for k, v in f.items()}, nthreads=THREADS)
@@ -149,6 +151,13 @@ def test_batched_64_patches(B, orc, report):
         assert abs(dts[p] - ref.dt) <= 1e-12 * ref.dt, (p, dts[p], ref.dt)
         assert np.abs(x[a:b] - ref["x"]).max() <= 1e-12 * max(1.0, np.abs(ref["x"]).max()), p
         assert np.abs(hh[a:b] - ref["h"]).max() <= 1e-12 * np.abs(ref["h"]).max(), p
+        # all 7 conserved sums of each patch after its own step
+        ce = conserved_errors(cons[p], ref.conserved(),
+                              conserved_scales(*[ref[k] for k in ("x", "y", "vx", "vy", "vz", "m", "u")]))
+        for k, v in ce.items():
+            assert v < 1e-12, (p, k, v)
+        worst_c = max(worst_c, max(ce.values()))
+    report["fullsize/batched64"]["conserved_fp64"] = worst_c
 
 
 def test_full_size_fused_matches_lists(B):

@@ -81,7 +81,7 @@ def test_fused_pair_sums_match_oracle(B, orc, case, precision, tol, report):
     _check_forces(g, o, tol, report, "fused/%s/%s" % (precision, case))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_fused_ten_steps(B, orc, precision, tol, report):
     """Ten steps without any list: against the oracle, and bit for bit
     against the list mode with one lane per particle."""

@@ -81,7 +81,7 @@ def test_every_step_exact(B, orc, case, precision, tol, skin, report):
         assert r < nsteps, "a skin of 0.25 should carry the superset over some steps"
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_reuse_trajectory(B, orc, precision, tol, report):
     f = inputs.square_patch(20)
     n = len(f["x"])

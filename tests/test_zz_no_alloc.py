@@ -35,8 +35,8 @@ def _fields(n, seed):
 def _scales(f):
     """Per sum, the sum of its terms' magnitudes: the scale of its rounding."""
     m = f["m"]
-    return np.array([m.sum(), (m * np.abs(f["vx"])).sum(), (m * np.abs(f["vy"])).sum(),
-                     (m * np.abs(f["vz"])).sum(),
+    pv = (m * np.sqrt(f["vx"] ** 2 + f["vy"] ** 2 + f["vz"] ** 2)).sum()
+    return np.array([m.sum(), pv, pv, pv,
                      (m * (np.abs(f["x"] * f["vy"]) + np.abs(f["y"] * f["vx"]))).sum(),
                      (0.5 * m * (f["vx"] ** 2 + f["vy"] ** 2 + f["vz"] ** 2)).sum(),
                      (m * np.abs(f["u"])).sum()])
