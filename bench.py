@@ -272,6 +272,9 @@ def main():
                     help="fixed cell factor (implies --no-autotune); 0 = tuned")
     ap.add_argument("--tpp", type=int, default=0,
                     help="fixed lanes per particle of the pair sums (implies --no-autotune); 0 = tuned")
+    ap.add_argument("--pair-bins", type=int, default=0,
+                    help="row-length bins of the pair sums, list words per lane (8..256; -1: never; "
+                         "0: the autotuner decides)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.cell_factor or args.tpp:
@@ -311,6 +314,8 @@ def main():
             kw["cell_factor"] = args.cell_factor
         if args.tpp:
             kw["threads_per_particle"] = args.tpp
+        if args.pair_bins:
+            kw["pair_bins"] = args.pair_bins
         kw.update(over)
         sim = binding.SPH(n, precision=precision, stream=stream.cuda_stream, use_graph=int(graph),
                           max_pairs=int(160 * n), max_patches=64 if offsets is not None else 1, **kw)
@@ -332,6 +337,7 @@ def main():
         sim.step(1)
     tpp, cf = binding.sph_get_tuning(sim.ctx)
     tpp_den = binding.sph_get_density_tpp(sim.ctx)
+    bins_den, bins_mom = sim.pair_bins()
     mode = sim.pair_mode()
     torch.cuda.synchronize()
     # the state at the start of the timed steps, on the host: the end-to-end
@@ -458,6 +464,8 @@ def main():
                    "l2": "inputs larger than L2 (%.1f GB of particle fields and neighbour lists)"
                          % ((n * 13 * 8 * 2 + pairs_per_step * 4) / 1e9),
                    "threads_per_particle": tpp, "threads_per_particle_density": tpp_den,
+                   "row_length_bins": {"density_words_per_lane": bins_den, "momentum_words_per_lane": bins_mom,
+                                       "note": "0: uniform lanes per particle"},
                    "cell_factor": cf, "pair_mode": mode,
                    "list_skin": args.skin, "searches_in_timed_steps": rebuilds if args.skin > 0 else args.steps,
                    "timed": "K steps with CUDA events between phases (no graph)"},

@@ -60,7 +60,7 @@ enum { SPH_KERNEL_WENDLAND = 0, SPH_KERNEL_SINC = 1 }; /* sph_config.kernel */
 
 /* How the pair sums find their pairs (sph_config.pair_mode). */
 enum {
-    SPH_PAIRS_LISTS = 0,    /* the step writes neighbour lists (A4) and the
+    SPH_PAIRS_LISTS = 0,    /* the step writes neighbour lists and the
                                density and momentum sums read them */
     SPH_PAIRS_FUSED = 1,    /* no lists: the density and the momentum sums each
                                run the neighbour search themselves and take
@@ -134,6 +134,19 @@ typedef struct {
                                with a margin over their previous length. */
     int32_t max_patches;    /* capacity of independent patches, <= 256 */
     int32_t use_graph;      /* 1: sph_step replays a captured CUDA graph */
+    int32_t pair_bins;      /* load balance of the pair sums over lists of
+                               uneven length (the imbalance Sec. 4.2 finds
+                               across ranks, here across the lanes of a
+                               warp): the particles are binned by row-length
+                               octave after each search and each octave is
+                               summed with the lanes per particle that keep a
+                               lane at pair_bins list words or fewer (8, 16,
+                               32, 64, 128 or 256; 1 to 32 lanes), so the rows
+                               summed side by side differ by less than 2x.
+                               0 (default): uniform lanes until sph_autotune,
+                               which times bins against uniform lanes;
+                               -1: never bins */
+    int32_t reserved;       /* set to 0 */
     void* cuda_stream;      /* cudaStream_t or NULL */
 } sph_config;
 
@@ -267,6 +280,11 @@ sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* c
 /* Lanes per particle of the density sum (sph_autotune tunes it apart from the
  * momentum sum's). */
 sph_status sph_get_density_tpp(sph_ctx* ctx, int32_t* threads_per_particle);
+
+/* Row-length bins in effect (sph_config.pair_bins, or the autotuner's
+ * choice): the list-word target per lane of the density and of the momentum
+ * sum, 0 where that sum runs with uniform lanes per particle. */
+sph_status sph_get_pair_bins(sph_ctx* ctx, int32_t* words_density, int32_t* words_momentum);
 
 /* The pair mode in effect: SPH_PAIRS_LISTS or SPH_PAIRS_FUSED (SPH_PAIRS_AUTO
  * resolves to one of them in sph_autotune). */

@@ -39,6 +39,7 @@ class SphConfig(ctypes.Structure):
                 ("cell_factor", ctypes.c_double), ("list_skin", ctypes.c_double),
                 ("max_particles", ctypes.c_int64), ("max_pairs", ctypes.c_int64),
                 ("max_patches", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("pair_bins", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p)]
 
 
@@ -80,6 +81,7 @@ SIGNATURES = {
     "sph_get_tuning": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
     "sph_get_pair_mode": (_ST, [_P, ctypes.POINTER(_I32)]),
     "sph_get_density_tpp": (_ST, [_P, ctypes.POINTER(_I32)]),
+    "sph_get_pair_bins": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sph_get_list_rebuilds": (_ST, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "sph_set_profiling": (_ST, [_P, ctypes.c_int]),
     "sph_get_profile": (_ST, [_P, _P, _P, _I32]),
@@ -315,6 +317,14 @@ def sph_get_pair_mode(ctx):
     return "fused" if m.value == SPH_PAIRS_FUSED else "lists"
 
 
+def sph_get_pair_bins(ctx):
+    """(density, momentum): list words per lane of the row-length bins of each
+    pair sum, 0 where the sum runs with uniform lanes per particle."""
+    d, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, lib().sph_get_pair_bins(ctx, ctypes.byref(d), ctypes.byref(m)))
+    return d.value, m.value
+
+
 def sph_get_density_tpp(ctx):
     """Lanes per particle of the density sum."""
     v = ctypes.c_int32()
@@ -511,6 +521,9 @@ class SPH:
 
     def pair_mode(self):
         return sph_get_pair_mode(self.ctx)
+
+    def pair_bins(self):
+        return sph_get_pair_bins(self.ctx)
 
     def list_rebuilds(self):
         return sph_get_list_rebuilds(self.ctx)

@@ -90,6 +90,12 @@ struct sph_ctx {
     int npatch = 0, nitems = 0, radix_passes = 3;
     int tpp_pair = 8;              // lanes per particle of the momentum sum
     int tpp_den = 8;               // ... and of the density sum
+    // row-length bins of the pair sums: log2 of the list words per lane
+    // (0: every particle with the uniform tpp above)
+    int bins_pair = 0, bins_den = 0;
+    uint32_t* bin_order = nullptr; // particles sorted stably by row-length octave
+    uint32_t* bin_bounds = nullptr; // [kPairOctaves + 1] octave starts in bin_order
+    bool bins_valid = false;       // bin_order belongs to the current lists
     double cell_factor = 0.5;
     int mixed = 1;
     bool fused = false;            // pair sums without lists (SPH_PAIRS_FUSED in effect)
@@ -334,6 +340,9 @@ PairArgs pair_args(sph_ctx* ctx)
     a.grad_h = ctx->cfg.grad_h;
     a.kb = ctx->kernel_b;
     a.status = ctx->status;
+    a.order = nullptr;
+    a.bounds = nullptr;
+    a.bin_lo = a.bin_hi = 0;
     return a;
 }
 
@@ -422,8 +431,27 @@ void enqueue_lists(sph_ctx* ctx)
         Phase p(ctx, SPH_PHASE_NB);
         ctx->launches += launch_nb_lists(L, a, stencil_k(ctx->cell_factor), 1);
     }
+    ctx->bins_valid = false;
     // the row lengths now belong to the current order: hints for the next sort
     cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
+}
+
+// the particles binned by row length, once per set of lists (counted in the
+// phase that first needs them)
+void enqueue_bins(sph_ctx* ctx)
+{
+    if (ctx->bins_valid) return;
+    ctx->launches += launch_pair_bins(launch_of(ctx), ctx->n, ctx->cnt, ctx->keys, ctx->bin_order, ctx->keys_alt,
+                                      ctx->vals_alt, ctx->hist, ctx->scan32, ctx->bin_bounds);
+    ctx->bins_valid = true;
+}
+
+PairArgs binned_args(sph_ctx* ctx)
+{
+    PairArgs a = pair_args(ctx);
+    a.order = ctx->bin_order;
+    a.bounds = ctx->bin_bounds;
+    return a;
 }
 
 void enqueue_density(sph_ctx* ctx)
@@ -442,7 +470,12 @@ void enqueue_density(sph_ctx* ctx)
         return;
     }
     Phase p(ctx, SPH_PHASE_DENSITY);
-    ctx->launches += launch_density(launch_of(ctx), pair_args(ctx), ctx->tpp_den, ctx->mixed);
+    if (ctx->bins_den) {
+        enqueue_bins(ctx);
+        ctx->launches += launch_density_binned(launch_of(ctx), binned_args(ctx), ctx->bins_den, ctx->mixed);
+    } else {
+        ctx->launches += launch_density(launch_of(ctx), pair_args(ctx), ctx->tpp_den, ctx->mixed);
+    }
 }
 
 void enqueue_momentum(sph_ctx* ctx)
@@ -451,8 +484,12 @@ void enqueue_momentum(sph_ctx* ctx)
     if (ctx->fused)
         ctx->launches += launch_fused_momentum(launch_of(ctx), nb_args(ctx), pair_args(ctx),
                                                stencil_k(ctx->cell_factor), ctx->mixed);
-    else
+    else if (ctx->bins_pair) {
+        enqueue_bins(ctx);
+        ctx->launches += launch_momentum_binned(launch_of(ctx), binned_args(ctx), ctx->bins_pair, ctx->mixed);
+    } else {
         ctx->launches += launch_momentum(launch_of(ctx), pair_args(ctx), ctx->tpp_pair, ctx->mixed);
+    }
 }
 
 // the candidate superset of reused lists on the grid of the last sort (its
@@ -496,6 +533,7 @@ void enqueue_filter(sph_ctx* ctx)
         Phase p(ctx, SPH_PHASE_NB);
         ctx->launches += launch_nb_filter(L, nb_args(ctx), ctx->col_s, ctx->cnt_s);
     }
+    ctx->bins_valid = false;
     cudaMemsetAsync(ctx->hint_ok, 1, sizeof(int), ctx->stream);
 }
 
@@ -679,6 +717,8 @@ void sph_config_default(sph_config* c)
     c->max_pairs = 0;
     c->max_patches = 1;
     c->use_graph = 0;
+    c->pair_bins = 0;
+    c->reserved = 0;
     c->cuda_stream = nullptr;
 }
 
@@ -749,6 +789,9 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     const int t = cfg.threads_per_particle;
     if (!(t == 0 || t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32))
         return fail(nullptr, SPH_EINVAL, "threads_per_particle must be 0, 1, 2, 4, 8, 16 or 32");
+    const int pb = cfg.pair_bins;
+    if (!(pb == 0 || pb == -1 || pb == 8 || pb == 16 || pb == 32 || pb == 64 || pb == 128 || pb == 256))
+        return fail(nullptr, SPH_EINVAL, "pair_bins must be 0, -1, 8, 16, 32, 64, 128 or 256");
     if (!(cfg.gamma > 1.0) || !(cfg.courant > 0.0) || !(cfg.dt_growth >= 1.0) || !(cfg.lz > 0.0) ||
         !(cfg.n_target > 0.0) || !(cfg.av_alpha >= 0.0) || !(cfg.av_beta >= 0.0) || !(cfg.av_eps > 0.0) ||
         !(cfg.dt_fixed >= 0.0))
@@ -780,6 +823,11 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ctx->kernel_b = kernel_norm(cfg.kernel, cfg.kernel_n);
     ctx->cell_factor = cfg.cell_factor;
     if (t) ctx->tpp_pair = ctx->tpp_den = t;
+    if (pb > 0) {
+        int w = 0;
+        while ((1 << w) < pb) w++;
+        ctx->bins_pair = ctx->bins_den = w;
+    }
     ctx->fused = cfg.pair_mode == SPH_PAIRS_FUSED;
     ctx->cap_n = cfg.max_particles;
     ctx->cap_patch = cfg.max_patches;
@@ -830,6 +878,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         double** g[14] = {&f.vhx, &f.vhy, &f.vhz, &f.rho, &f.P, &f.c, &f.A, &f.hc, &f.w, &f.w5, &f.ax, &f.ay, &f.az, &f.du};
         for (int k = 0; k < 14 && ok; k++) ok = dalloc(ctx, *g[k], N);
     }
+    ok = ok && dalloc(ctx, ctx->bin_order, N) && dalloc(ctx, ctx->bin_bounds, (size_t)kPairOctaves + 1);
     ok = ok && dalloc(ctx, ctx->cnt, N) && dalloc(ctx, ctx->cnt_orig, N) && dalloc(ctx, ctx->nown, N) &&
          dalloc(ctx, ctx->off, N + 1) &&
          dalloc(ctx, ctx->col, (size_t)ctx->pool_cap) && dalloc(ctx, ctx->rowcap, N);
@@ -1354,41 +1403,81 @@ sph_status sph_autotune(sph_ctx* ctx)
         }
         return best;
     };
-    // lists: the search writing them plus the best lanes-per-particle of the
-    // sums over them; list-free: the two passes (each runs the search)
+    // lists: the search writing them plus the best launch shape of each sum
+    // over them (a uniform lanes-per-particle count, or row-length bins with
+    // a words-per-lane target, whose binning pass is paid once per step);
+    // list-free: the two passes (each runs the search)
     const bool try_lists = ctx->cfg.pair_mode != SPH_PAIRS_FUSED;
     const bool try_fused = ctx->cfg.pair_mode != SPH_PAIRS_LISTS;
+    const bool fixed_bins = ctx->cfg.pair_bins > 0;
+    const bool try_bins = ctx->cfg.pair_bins == 0;
+    const int bin_ws[4] = {4, 5, 6, 7};   // 16 .. 128 list words per lane
     double best_total = 1e300, best_f = ctx->cell_factor;
     int best_pair = ctx->tpp_pair, best_den = ctx->tpp_den;
+    int best_bpair = ctx->bins_pair, best_bden = ctx->bins_den;
     bool best_fused = ctx->fused;
     for (double f : factors) {
         ctx->cell_factor = f;
         enqueue_sort(ctx);
         if (try_lists) {
             ctx->fused = false;
-            float bden = 1e30f, bmom = 1e30f;
-            int tden = 8, tmom = 8;
             const float bnb = timeit([&] { enqueue_lists(ctx); });
-            // the two sums separately (the momentum sum reads the density's records)
-            for (int t : pair_tpps) {
-                ctx->tpp_den = t;
-                const float ms = timeit([&] { enqueue_density(ctx); });
-                if (ms < bden) { bden = ms; tden = t; }
+            // uniform shapes
+            float uden = 1e30f, umom = 1e30f, bden = 1e30f, bmom = 1e30f;
+            int tden = 8, tmom = 8, wden = 0, wmom = 0;
+            if (!fixed_bins) {
+                ctx->bins_den = ctx->bins_pair = 0;
+                for (int t : pair_tpps) {
+                    ctx->tpp_den = t;
+                    const float ms = timeit([&] { enqueue_density(ctx); });
+                    if (ms < uden) { uden = ms; tden = t; }
+                }
             }
+            float tbin = 0.0f;
+            if (try_bins || fixed_bins) {
+                tbin = timeit([&] { ctx->bins_valid = false; enqueue_bins(ctx); });
+                for (int w : bin_ws) {
+                    if (fixed_bins && w != ctx->bins_den) continue;
+                    ctx->bins_den = w;
+                    const float ms = timeit([&] { enqueue_density(ctx); });
+                    if (ms < bden) { bden = ms; wden = w; }
+                }
+                if (fixed_bins) wden = ctx->bins_den;
+            }
+            // the momentum sum reads the density's records: one density sum first
+            ctx->bins_den = 0;
             ctx->tpp_den = tden;
             enqueue_density(ctx);
-            for (int t : pair_tpps) {
-                ctx->tpp_pair = t;
-                const float ms = timeit([&] { enqueue_momentum(ctx); });
-                if (ms < bmom) { bmom = ms; tmom = t; }
+            if (!fixed_bins) {
+                ctx->bins_pair = 0;
+                for (int t : pair_tpps) {
+                    ctx->tpp_pair = t;
+                    const float ms = timeit([&] { enqueue_momentum(ctx); });
+                    if (ms < umom) { umom = ms; tmom = t; }
+                }
             }
-            const double tot = (double)bnb + (double)bden + (double)bmom;
-            if (tot < best_total) {
-                best_total = tot;
-                best_f = f;
-                best_pair = tmom;
-                best_den = tden;
-                best_fused = false;
+            if (try_bins || fixed_bins) {
+                for (int w : bin_ws) {
+                    if (fixed_bins && w != ctx->bins_pair) continue;
+                    ctx->bins_pair = w;
+                    const float ms = timeit([&] { enqueue_momentum(ctx); });
+                    if (ms < bmom) { bmom = ms; wmom = w; }
+                }
+            }
+            // the four combinations of uniform and binned sums
+            for (int c = 0; c < 4; c++) {
+                const bool bd = c & 1, bm = c & 2;
+                if ((bd && !wden) || (bm && !wmom) || (!bd && uden >= 1e29f) || (!bm && umom >= 1e29f)) continue;
+                const double tot = (double)bnb + (bd ? bden : uden) + (bm ? bmom : umom) + ((bd || bm) ? tbin : 0.0f);
+                if (tot < best_total) {
+                    best_total = tot;
+                    best_f = f;
+                    best_den = tden;
+                    best_pair = tmom;
+                    best_bden = bd ? wden : 0;
+                    best_bpair = bm ? wmom : 0;
+                    best_fused = false;
+                }
             }
         }
         if (try_fused) {
@@ -1406,6 +1495,9 @@ sph_status sph_autotune(sph_ctx* ctx)
     ctx->cell_factor = best_f;
     ctx->tpp_pair = best_pair;
     ctx->tpp_den = best_den;
+    ctx->bins_pair = best_bpair;
+    ctx->bins_den = best_bden;
+    ctx->bins_valid = false;
     ctx->fused = best_fused;
     ctx->prof = prof0;
     ctx->nb_valid = ctx->rho_valid = ctx->acc_valid = ctx->sup_valid = false;
@@ -1428,6 +1520,14 @@ sph_status sph_get_density_tpp(sph_ctx* ctx, int32_t* tpp)
 {
     if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
     if (tpp) *tpp = ctx->tpp_den;
+    return SPH_OK;
+}
+
+sph_status sph_get_pair_bins(sph_ctx* ctx, int32_t* words_density, int32_t* words_momentum)
+{
+    if (!ctx) return fail(nullptr, SPH_EINVAL, "null context");
+    if (words_density) *words_density = ctx->bins_den ? 1 << ctx->bins_den : 0;
+    if (words_momentum) *words_momentum = ctx->bins_pair ? 1 << ctx->bins_pair : 0;
     return SPH_OK;
 }
 

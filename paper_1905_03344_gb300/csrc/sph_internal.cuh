@@ -256,9 +256,35 @@ struct PairArgs {
     int grad_h;                          // 1: grad-h form (density stores A/Omega)
     double kb;                           // sigma_W (Wendland) or B_n (Sinc)
     int* status;
+    // row-length bins (nullptr order: every particle, in sorted order): the
+    // launch takes positions bounds[bin_lo] .. bounds[bin_hi + 1] of order,
+    // the particles whose rows fall in those octaves
+    const uint32_t* order;
+    const uint32_t* bounds;
+    int bin_lo, bin_hi;
 };
 int launch_density(const Launch& L, const PairArgs& a, int tpp, int mixed);
 int launch_momentum(const Launch& L, const PairArgs& a, int tpp, int mixed);
+// Row-length bins: octave 0 holds the empty rows, octave o >= 1 the rows with
+// |N(i)| in (2^(o-2), 2^(o-1)], o < kPairOctaves (the last octave takes every
+// longer row).  With a target of 2^w list words per lane, octave o gets
+// clamp(2^(o-1-w), 1, 32) lanes per particle -- the smallest power of two
+// that keeps a lane at 2^w words or fewer -- and the rows of one launch's
+// warps differ by less than 2x.
+constexpr int kPairOctaves = 16;
+__host__ __device__ __forceinline__ int octave_tpp(int o, int w)
+{
+    const int e = o - 1 - w;
+    return e <= 0 ? 1 : (e >= 5 ? 32 : 1 << e);
+}
+// order = the particles stably sorted by octave (sorted order kept inside
+// each octave), bounds[o] = first position of octave o, bounds[kPairOctaves] = n
+int launch_pair_bins(const Launch& L, int64_t n, const uint32_t* cnt, uint32_t* keys, uint32_t* order,
+                     uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist, uint32_t* scan_tmp, uint32_t* bounds);
+// the sums over row-length bins with 2^w words per lane (one launch per
+// distinct lanes-per-particle value)
+int launch_density_binned(const Launch& L, PairArgs a, int w, int mixed);
+int launch_momentum_binned(const Launch& L, PairArgs a, int w, int mixed);
 // list-free pair sums over the search of the current grid (stencil
 // half-extent K); the density pass also writes |N(i)| and n_i and adds the
 // pairs to pool_used[1]

@@ -49,6 +49,26 @@ __device__ __forceinline__ RowAhead row_ahead_read(const PairArgs& a, int64_t i)
     return r;
 }
 
+// the positions [kb, ke) a launch covers: every particle, or a range of
+// row-length bins of the order
+__device__ __forceinline__ void pair_range(const PairArgs& a, int64_t& kb, int64_t& ke)
+{
+    if (a.order) {
+        kb = a.bounds[a.bin_lo];
+        ke = a.bounds[a.bin_hi + 1];
+    } else {
+        kb = 0;
+        ke = a.n;
+    }
+}
+
+// the particle at position k (a.n past the range: no particle)
+__device__ __forceinline__ int64_t pair_at(const PairArgs& a, int64_t k, int64_t ke)
+{
+    if (k >= ke) return a.n;
+    return a.order ? (int64_t)a.order[k] : k;
+}
+
 template <int TPP>
 __device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowAhead& r, int gl)
 {
@@ -95,11 +115,14 @@ __global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const float gam = (float)a.gamma;
-    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
-    RowAhead ahead = row_ahead_read(a, i0 + gs);
-    for (int64_t i = i0; i < a.n; i += gs) {
+    int64_t kb, ke;
+    pair_range(a, kb, ke);
+    const int64_t k0 = kb + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+    RowAhead ahead = row_ahead_read(a, pair_at(a, k0 + gs, ke));
+    for (int64_t k = k0; k < ke; k += gs) {
+        const int64_t i = pair_at(a, k, ke);
         row_ahead_prefetch<TPP>(a, ahead, G.gl);
-        ahead = row_ahead_read(a, i + 2 * gs);
+        ahead = row_ahead_read(a, pair_at(a, k + 2 * gs, ke));
         const PatchDev* P = a.pd + a.patch_of[i];
         const PairSide I = pair_side(a, P, i);
         const float inv2h = a.r.rv[i].w;                   // 1 / (2 h_i)
@@ -124,7 +147,10 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
     if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+    int64_t kb, ke;
+    pair_range(a, kb, ke);
+    for (int64_t k = kb + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; k < ke; k += gs) {
+        const int64_t i = pair_at(a, k, ke);
         const PatchDev* P = a.pd + a.patch_of[i];
         const double xi = a.s.x[i], yi = a.s.y[i], zi = a.s.z[i];
         const double w = a.f.w[i];
@@ -183,11 +209,14 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const MomConst K = {0.25f * (float)a.eps, 0.5f * (float)a.beta, 0.5f * (float)a.alpha};
-    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
-    RowAhead ahead = row_ahead_read(a, i0 + gs);
-    for (int64_t i = i0; i < a.n; i += gs) {
+    int64_t kb, ke;
+    pair_range(a, kb, ke);
+    const int64_t k0 = kb + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+    RowAhead ahead = row_ahead_read(a, pair_at(a, k0 + gs, ke));
+    for (int64_t k = k0; k < ke; k += gs) {
+        const int64_t i = pair_at(a, k, ke);
         row_ahead_prefetch<TPP>(a, ahead, G.gl);
-        ahead = row_ahead_read(a, i + 2 * gs);
+        ahead = row_ahead_read(a, pair_at(a, k + 2 * gs, ke));
         const PatchDev* P = a.pd + a.patch_of[i];
         const PairSide I = pair_side(a, P, i);
         const float4 vi = a.r.rv[i];
@@ -218,7 +247,10 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
     const int kn = a.kernel_n;
     const double S80 = KernF<KERN>::grad_scale(a.kb, kn);
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; i < a.n; i += gs) {
+    int64_t kb, ke;
+    pair_range(a, kb, ke);
+    for (int64_t k = kb + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP; k < ke; k += gs) {
+        const int64_t i = pair_at(a, k, ke);
         const PatchDev* P = a.pd + a.patch_of[i];
         const SideD I = side_fp64(a, P, i);
         const uint32_t* row = a.col + a.rowstart[i];
@@ -292,6 +324,37 @@ int launch_momentum(const Launch& L, const PairArgs& a, int tpp, int mixed)
         SPH_DISPATCH(k_momentum_fp64, tpp, blocks, L, a);
     }
     return 1;
+}
+
+// One launch per run of octaves that share a lanes-per-particle value (the
+// bin sizes stay on the device, so every launch takes the full grid and
+// strides over its range; a launch whose range is empty returns at once).
+template <class F>
+static int binned_launches(PairArgs a, int w, F&& launch_one)
+{
+    if (a.n <= 0 || !a.order) return 0;
+    int launches = 0;
+    int o = 0;
+    while (o < kPairOctaves) {
+        const int t = octave_tpp(o, w);
+        int e = o;
+        while (e + 1 < kPairOctaves && octave_tpp(e + 1, w) == t) e++;
+        a.bin_lo = o;
+        a.bin_hi = e;
+        launches += launch_one(a, t);
+        o = e + 1;
+    }
+    return launches;
+}
+
+int launch_density_binned(const Launch& L, PairArgs a, int w, int mixed)
+{
+    return binned_launches(a, w, [&](const PairArgs& b, int t) { return launch_density(L, b, t, mixed); });
+}
+
+int launch_momentum_binned(const Launch& L, PairArgs a, int w, int mixed)
+{
+    return binned_launches(a, w, [&](const PairArgs& b, int t) { return launch_momentum(L, b, t, mixed); });
 }
 
 }  // namespace sphg

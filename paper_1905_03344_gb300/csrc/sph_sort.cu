@@ -565,6 +565,50 @@ int launch_radix_sort(const Launch& L, int64_t n, int passes, uint32_t* keys, ui
 }
 
 // ---------------------------------------------------------------------------
+// Row-length bins of the pair sums: key = octave of |N(i)|, sorted stably by
+// one radix pass; the bin starts are the scanned digit offsets of the first
+// tile.
+// ---------------------------------------------------------------------------
+__global__ void k_octave_keys(int64_t n, const uint32_t* cnt, uint32_t* keys, uint32_t* vals)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[i];
+        // 0 for an empty row, else 1 + ceil(log2 c) (32 - clz(c - 1) = ceil(log2 c))
+        const int o = c == 0u ? 0 : 33 - __clz(c - 1u);
+        keys[i] = (uint32_t)min(o, kPairOctaves - 1);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_octave_bounds(const uint32_t* hist, int ntiles, int64_t n, uint32_t* bounds)
+{
+    const int o = threadIdx.x;
+    if (o < kPairOctaves) bounds[o] = hist[(int64_t)o * ntiles];
+    if (o == kPairOctaves) bounds[o] = (uint32_t)n;
+}
+
+int launch_pair_bins(const Launch& L, int64_t n, const uint32_t* cnt, uint32_t* keys, uint32_t* order,
+                     uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist, uint32_t* scan_tmp, uint32_t* bounds)
+{
+    if (n <= 0) return 0;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)L.sms * 16) blocks = (int64_t)L.sms * 16;
+    k_octave_keys<<<(unsigned)blocks, 256, 0, L.stream>>>(n, cnt, keys, order);
+    int launches = 1;
+    const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
+    if (n > 1) {
+        launches += launch_radix_sort(L, n, 1, keys, order, keys_alt, vals_alt, hist, scan_tmp);
+    } else {
+        // one particle, no sort: every bound but the last is 0, so it is
+        // summed by the last octave's launch (any lanes-per-particle count
+        // gives a correct sum)
+        cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256, L.stream);
+    }
+    k_octave_bounds<<<1, 32, 0, L.stream>>>(hist, ntiles, n, bounds);
+    return launches + 1;
+}
+
+// ---------------------------------------------------------------------------
 // Gather every field into sorted order, write the permutation, the
 // cell table (start/end by key boundaries, largest h per cell) and the FP32
 // records with positions relative to the particle's cell origin.  Also forms

@@ -101,11 +101,30 @@ def test_full_size_patch(B, orc, name, report):
     sim.momentum_energy()
     g = {k: sim.field(k) for k in ("rho", "P", "c", "ax", "ay", "az", "du")}
     tpp, cf = B.sph_get_tuning(sim.ctx)
+    bins = sim.pair_bins()
     sim.close()
     errs = force_errors(g, o)
-    report["fullsize/%s" % name] = dict(errs, tpp=tpp, cell_factor=cf, n=n, nnz=int(nb.off[-1]))
+    report["fullsize/%s" % name] = dict(errs, tpp=tpp, cell_factor=cf, bins=bins, n=n, nnz=int(nb.off[-1]))
     for k, v in errs.items():
         assert v < TOL_MIXED, (name, k, v)
+    if name == "c5":
+        # row-length bins with 16 words per lane: the irregular patch's rows
+        # (~50-400) fill the octaves of 4, 8, 16 and 32 lanes per particle
+        rows = np.diff(nb.off)
+        tpps = {min(32, max(1, 1 << int(np.ceil(np.log2(max(c, 1) / 16.0))))) for c in np.unique(rows)}
+        assert {4, 8, 16, 32} <= tpps, sorted(tpps)
+        sb = B.SPH(n, precision="mixed", max_pairs=160 * n, pair_bins=16)
+        sb.set_particles(f)
+        sb.find_neighbors()
+        sb.density()
+        sb.momentum_energy()
+        gb = {k: sb.field(k) for k in ("rho", "P", "c", "ax", "ay", "az", "du")}
+        assert sb.pair_bins() == (16, 16)
+        sb.close()
+        errs = force_errors(gb, o)
+        report["fullsize/c5/bins16"] = errs
+        for k, v in errs.items():
+            assert v < TOL_MIXED, ("c5 bins", k, v)
 
 
 def test_batched_64_patches(B, orc, report):

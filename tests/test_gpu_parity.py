@@ -167,6 +167,45 @@ def test_mixed_pair_sums(B, orc, case, tpp, report):
 
 
 @pytest.mark.parametrize("case", sorted(FORCE_CASES))
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+@pytest.mark.parametrize("words", [8, 64])
+def test_binned_pair_sums(B, orc, case, precision, tol, words, report):
+    """Row-length bins: each octave of row lengths summed with its own lanes
+    per particle, against the oracle."""
+    f = FORCE_CASES[case]()
+    lz = f.pop("lz", 1.0)
+    _check_forces(_gpu_forces(B, f, precision, pair_bins=words, lz=lz), _oracle_forces(orc, f, lz), tol,
+                  report, "bins%d/%s/%s" % (words, precision, case))
+
+
+def _octave_tpp(c, words):
+    """Lanes per particle of a row of c words with a target of `words` per lane."""
+    return min(32, max(1, 1 << int(np.ceil(np.log2(max(c, 1) / words))))) if c > words else 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_binned_sums_are_the_uniform_sums_of_each_octave(B, orc, precision):
+    """A particle's binned density sum is, bit for bit, that of a uniform
+    launch with its octave's lanes per particle: the bins change which lanes
+    sum a row, never the row.  (The momentum sum reads its neighbours'
+    densities, which differ between such runs; it is checked against the
+    oracle above.)  In this cloud h grows by e^2 from one side to the other,
+    so rows run from 0 to ~190 words and, with 8 words per lane, every
+    lanes-per-particle value 1..32 occurs."""
+    f = inputs.random_cloud(3000, seed=2)
+    f["h"] = 0.02 * np.exp(2.0 * (f["x"] + 0.5))
+    rows = np.diff(orc.neighbors(f["x"], f["y"], f["z"], f["h"]).off)
+    want = np.array([_octave_tpp(int(c), 8) for c in rows])
+    assert set(want) == {1, 2, 4, 8, 16, 32}
+    keys = ("rho", "P", "c")
+    binned = _gpu_forces(B, dict(f), precision, pair_bins=8)
+    uni = {t: _gpu_forces(B, dict(f), precision, threads_per_particle=t, pair_bins=-1) for t in (1, 2, 4, 8, 16, 32)}
+    for k in keys:
+        pick = np.choose(np.log2(want).astype(int), [uni[t][k] for t in (1, 2, 4, 8, 16, 32)])
+        assert np.array_equal(binned[k].view(np.uint64), pick.view(np.uint64)), k
+
+
+@pytest.mark.parametrize("case", sorted(FORCE_CASES))
 def test_mixed_pair_sums_small_cells(B, orc, case, report):
     """Cells of a third of 2 h_s: neighbours three cells away carry the far
     column code and take their offsets from the cell coordinates."""
