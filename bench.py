@@ -56,15 +56,14 @@ FLOPS_PER_PAIR_MOMENTUM_FP64 = 56
 # (4 B) read once.
 NB_BYTES_PER_ENTRY = 4
 NB_BYTES_PER_PARTICLE = 48
-# DRAM bytes (read + write) per list entry of one launch, from the ncu
-# capture of the same kernels on the 100^3 patch (dram__bytes_read.sum +
-# dram__bytes_write.sum divided by the launch's 1.024e8 list entries;
-# profiles/k_nb_thread_square_patch_100cubed.md and
-# profiles/k_momentum_mixed_square_patch_100cubed.md), scaled to the
-# benchmark's launch by its entries.  None once the kernel has changed since;
-# the momentum figure is that of its 2-lanes-per-particle instantiation.
-NB_DRAM_BYTES_PER_ENTRY = 5.91
-MOMENTUM_DRAM_BYTES_PER_ENTRY = 6.61
+# DRAM bytes (read + write) per list entry of one launch, from one-pass ncu
+# captures of these kernels on the 200^3 patch itself (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the launch's 8.54e8 list entries; see
+# profiles/launches_square_patch_200cubed.md), scaled to the benchmark's
+# launch by its entries.  None once the kernel has changed since; the
+# momentum figure is that of its 2-lanes-per-particle instantiation.
+NB_DRAM_BYTES_PER_ENTRY = 5.70
+MOMENTUM_DRAM_BYTES_PER_ENTRY = 7.89
 MOMENTUM_DRAM_TPP = 2
 
 WORKLOADS = {

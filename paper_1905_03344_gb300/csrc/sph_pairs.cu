@@ -30,7 +30,9 @@ namespace sphg {
 #define SPH_ROW_PREFETCH 1              // L2 prefetch of the next particle's row
 #endif
 
-// The list words stream from HBM (the pool is far larger than L2).  Each
+// The list words stream from HBM (the pool is far larger than L2) and are
+// read with the streaming hint (evict first), which leaves L2 to the
+// neighbour records every row gathers.  Each
 // group asks L2 for the row of the particle it takes next -- the group's lanes
 // cover it in 128-byte lines -- while it works on the current one; the start
 // of that row was read one particle earlier, so the request does not wait.
@@ -94,7 +96,7 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
         uint32_t cw[4];
         float4 q[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) cw[u] = row[min(k + (uint32_t)(u * TPP), len - 1u)];
+        for (int u = 0; u < 4; u++) cw[u] = __ldcs(row + min(k + (uint32_t)(u * TPP), len - 1u));
 #pragma unroll
         for (int u = 0; u < 4; u++) q[u] = src.r5[cw[u] & kColMask];
         // (the loads past the row end repeat its last word; they are not summed)
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
         const uint32_t len = a.cnt[i];
         double sum = 0.0, sumd = 0.0;
         for (uint32_t k = G.gl; k < len; k += TPP)
-            density_pair_fp64<KERN, GH>(a, xi, yi, zi, w, P->lz, kn, row[k] & kColMask, sum, sumd);
+            density_pair_fp64<KERN, GH>(a, xi, yi, zi, w, P->lz, kn, __ldcs(row + k) & kColMask, sum, sumd);
         sum = group_sum<TPP>(sum, G.gmask);
         if (GH) sumd = group_sum<TPP>(sumd, G.gmask);
         if (G.gl == 0) density_finish_fp64<GH>(a, i, sum, sumd);
@@ -184,9 +186,9 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
     const uint4* row4 = reinterpret_cast<const uint4*>(row);
     const uint32_t nch = (len + 3u) >> 2;
     uint32_t ch = (uint32_t)gl;
-    uint4 w = ch < nch ? row4[ch] : make_uint4(0u, 0u, 0u, 0u);
+    uint4 w = ch < nch ? __ldcs(row4 + ch) : make_uint4(0u, 0u, 0u, 0u);
     for (; ch < nch; ch += TPP) {
-        const uint4 wn = ch + TPP < nch ? row4[ch + TPP] : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 wn = ch + TPP < nch ? __ldcs(row4 + ch + TPP) : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t cws[4] = {w.x, w.y, w.z, w.w};
         const uint32_t nv = min(len - ch * 4u, 4u);
         float bx, by, bz, bu;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(256) k_momentum_fp64(PairArgs a)
         const uint32_t len = a.cnt[i];
         double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0;
         for (uint32_t k = G.gl; k < len; k += TPP) {
-            const PairTermsD t = momentum_pair_fp64<KERN, GH>(a, I, row[k] & kColMask, kn);
+            const PairTermsD t = momentum_pair_fp64<KERN, GH>(a, I, __ldcs(row + k) & kColMask, kn);
             ax += t.ax;
             ay += t.ay;
             az += t.az;

@@ -101,6 +101,11 @@ __device__ __forceinline__ int pair_decision(const NbArgs& a, const PatchDev* P,
 
 __device__ __forceinline__ uint32_t round8(uint32_t v) { return (v + 7u) & ~7u; }
 
+// The list words are written once and read back by the pair sums long after
+// (the pool is far larger than L2): they are stored with the streaming hint
+// (evict first), so that they do not push the candidate records, which every
+// lane re-reads, out of L2.
+//
 // the row being built by one lane; EXACT = false: every candidate that passed
 // the coarse FP32 test (the candidate superset of reused lists), no n_i
 template <int MODE, bool EXACT = true>
@@ -114,7 +119,7 @@ struct RowSink {
     __device__ __forceinline__ void put(uint32_t w)
     {
         if (MODE == kWalkRing) ring[(cnt & (kRing - 1)) * 32] = w;
-        else if (col) col[cnt] = w;
+        else if (col) __stcs(col + cnt, w);
         cnt++;
     }
     __device__ __forceinline__ uint32_t mark() const { return cnt; }
@@ -127,8 +132,8 @@ struct RowSink {
             if (blk + 8u <= res) {
                 const uint32_t* rg = ring + ((blk >> 3) & 1u) * (8 * 32);
                 uint4* dst = reinterpret_cast<uint4*>(col + blk);
-                dst[0] = make_uint4(rg[0], rg[32], rg[64], rg[96]);
-                dst[1] = make_uint4(rg[128], rg[160], rg[192], rg[224]);
+                __stcs(dst, make_uint4(rg[0], rg[32], rg[64], rg[96]));
+                __stcs(dst + 1, make_uint4(rg[128], rg[160], rg[192], rg[224]));
             }
         }
     }
@@ -136,7 +141,7 @@ struct RowSink {
     __device__ __forceinline__ void finish()
     {
         if (MODE == kWalkRing && cnt <= res)
-            for (uint32_t k = cnt & ~7u; k < cnt; k++) col[k] = ring[(k & (kRing - 1)) * 32];
+            for (uint32_t k = cnt & ~7u; k < cnt; k++) __stcs(col + k, ring[(k & (kRing - 1)) * 32]);
     }
     __device__ __forceinline__ void decide(const NbArgs& a, const PatchDev* P, int64_t i, uint32_t j, float r2,
                                            float Ti, float T, float flo, float fhi, uint32_t w)
