@@ -30,9 +30,10 @@ def _fields(n, **over):
     return f
 
 
+@pytest.mark.parametrize("bins", [0, 8])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_empty(B, precision):
-    sim = B.SPH(16, precision=precision)
+def test_empty(B, precision, bins):
+    sim = B.SPH(16, precision=precision, pair_bins=bins)
     sim.set_particles(_fields(0))
     sim.find_neighbors()
     off, col, perm = sim.neighbors()
@@ -42,9 +43,11 @@ def test_empty(B, precision):
     sim.close()
 
 
+@pytest.mark.parametrize("bins", [0, 8])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_single_particle(B, precision):
-    sim = B.SPH(4, precision=precision)
+def test_single_particle(B, precision, bins):
+    # with bins: one particle is no sort; it is summed by the last octave's launch
+    sim = B.SPH(4, precision=precision, pair_bins=bins)
     sim.set_particles(_fields(1, x=np.array([0.1]), vx=np.array([1.0])))
     sim.find_neighbors()
     sim.density()
@@ -58,9 +61,10 @@ def test_single_particle(B, precision):
     sim.close()
 
 
+@pytest.mark.parametrize("bins", [0, 8])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_coincident_pair(B, precision):
-    sim = B.SPH(4, precision=precision)
+def test_coincident_pair(B, precision, bins):
+    sim = B.SPH(4, precision=precision, pair_bins=bins)
     sim.set_particles(_fields(2))
     sim.find_neighbors()
     off, col, perm = sim.neighbors()
@@ -123,7 +127,8 @@ def test_bad_inputs(B):
                                 dict(max_particles=0), dict(gamma=1.0), dict(max_patches=300),
                                 dict(kernel=2), dict(kernel=1, kernel_n=1), dict(kernel=1, kernel_n=17),
                                 dict(grad_h=2), dict(grad_h=-1), dict(pair_mode=3), dict(pair_mode=-1),
-                                dict(list_skin=-0.1), dict(list_skin=1.5)])
+                                dict(list_skin=-0.1), dict(list_skin=1.5), dict(pair_bins=12), dict(pair_bins=-2),
+                                dict(pair_bins=512), dict(pair_bins=4)])
 def test_bad_config(B, kw):
     mp = kw.pop("max_particles", 8)
     with pytest.raises(B.SphError) as e:
@@ -201,13 +206,16 @@ def test_host_state_round_trip_every_step_bitwise(B, precision):
     ref.close()
 
 
+@pytest.mark.parametrize("bins", [0, 16])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_graph_replay_bitwise(B, precision):
+def test_graph_replay_bitwise(B, precision, bins):
+    """Replaying the captured step gives the same bits as launching it, also
+    with row-length bins (their bounds stay on the device)."""
     f = inputs.square_patch(12)
     n = len(f["x"])
     runs = []
     for graph in (0, 1):
-        sim = B.SPH(n, precision=precision, use_graph=graph)
+        sim = B.SPH(n, precision=precision, use_graph=graph, pair_bins=bins)
         sim.set_particles(f)
         sim.step(5)
         runs.append({k: sim.field(k) for k in ("x", "vy", "u", "h")})
