@@ -150,7 +150,9 @@ typedef struct {
     void* cuda_stream;      /* cudaStream_t or NULL */
 } sph_config;
 
-/* Fills the defaults listed above (max_particles = 1<<20, max_patches = 1). */
+/* Fills the defaults listed above (max_particles = 1<<20, max_patches = 1).
+ * The physical defaults are the readings of Sec. 3 (gamma = 5/3, C = 0.2,
+ * alpha = 1, beta = 2, 100 neighbours); the rest are library settings. */
 void sph_config_default(sph_config* cfg);
 
 /* One instance of the solver library the paper describes (its parts are
@@ -159,10 +161,12 @@ void sph_config_default(sph_config* cfg);
  * cfg.  Errors: SPH_EINVAL (bad cfg), SPH_ENOMEM, SPH_ECUDA (no device). */
 sph_status sph_create(const sph_config* cfg, sph_ctx** out);
 
-/* Frees everything; ctx may be NULL. */
+/* Frees everything; ctx may be NULL.  (Library housekeeping; no paper
+ * counterpart.) */
 void sph_destroy(sph_ctx* ctx);
 
-/* Message of the last failing call on ctx (ctx may be NULL: global message). */
+/* Message of the last failing call on ctx (ctx may be NULL: global message).
+ * (Library housekeeping; no paper counterpart.) */
 const char* sph_last_error(const sph_ctx* ctx);
 const char* sph_status_string(sph_status s);
 
@@ -198,7 +202,8 @@ sph_status sph_set_patches(sph_ctx* ctx, int32_t n_patches, const int64_t* offse
  * Errors: SPH_EOVERFLOW (more than max_pairs entries), SPH_ESTATE. */
 sph_status sph_find_neighbors(sph_ctx* ctx);
 
-/* Borrowed device pointers to the last neighbour lists as a canonical CSR in
+/* The result of the neighbour discovery of Table 1 as lists.
+ * Borrowed device pointers to the last neighbour lists as a canonical CSR in
  * sorted order: row k (sorted particle k) holds col[off[k] .. off[k+1]) as
  * sorted indices; perm[k] is the original index of sorted particle k.  Within
  * a row, the neighbours with h below the patch's class threshold come first,
@@ -210,7 +215,8 @@ sph_status sph_find_neighbors(sph_ctx* ctx);
 sph_status sph_get_neighbors(sph_ctx* ctx, const uint64_t** off, const uint32_t** col,
                              const uint32_t** perm, int64_t* nnz);
 
-/* Copies the last neighbour lists into caller buffers (device or host per
+/* The neighbour lists of Table 1's discovery, copied out.
+ * Copies the last neighbour lists into caller buffers (device or host per
  * on_device): off (n+1 uint64), col (nnz uint32, sorted indices), perm (n
  * uint32).  Any pointer may be NULL.  Same layout as sph_get_neighbors. */
 sph_status sph_copy_neighbors(sph_ctx* ctx, uint64_t* off, uint32_t* col, uint32_t* perm,
@@ -250,10 +256,13 @@ sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last);
  * computed in FP64 with a deterministic two-level reduction. */
 sph_status sph_conserved(sph_ctx* ctx, int32_t patch, double out[7]);
 
-/* Copies one field (SPH_FIELD_*) in original order into dst (n doubles). */
+/* Copies one field (SPH_FIELD_*) in original order into dst (n doubles): the
+ * particle state and the quantities of the Sec. 3 solver (rho, P, c, a,
+ * du/dt, n_i, |N(i)|). */
 sph_status sph_get_field(sph_ctx* ctx, int32_t field, double* dst, int on_device);
 
-/* Time state of a patch: last dt, the dt used as dt_{n-1}, steps taken. */
+/* Time state of a patch: last dt (the Courant step of Sec. 3), the dt used
+ * as dt_{n-1}, steps taken. */
 sph_status sph_get_dt(sph_ctx* ctx, int32_t patch, double* dt, double* dt_prev, int64_t* step);
 
 /* The mini-app has no checkpoint/restart (Table 2); the paper lists
@@ -273,28 +282,35 @@ sph_status sph_set_state(sph_ctx* ctx, const void* buf, size_t bytes);
  * particles and keeps the fastest; the particle state is left unchanged. */
 sph_status sph_autotune(sph_ctx* ctx);
 
-/* Current launch configuration (after sph_autotune or as configured): the
+/* No paper counterpart (launch settings of this library).
+ * Current launch configuration (after sph_autotune or as configured): the
  * momentum sum's lanes per particle and the cell factor. */
 sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* cell_factor);
 
-/* Lanes per particle of the density sum (sph_autotune tunes it apart from the
+/* No paper counterpart (launch settings of this library).
+ * Lanes per particle of the density sum (sph_autotune tunes it apart from the
  * momentum sum's). */
 sph_status sph_get_density_tpp(sph_ctx* ctx, int32_t* threads_per_particle);
 
-/* Row-length bins in effect (sph_config.pair_bins, or the autotuner's
+/* The load-balance settings for the imbalance Sec. 4.2 describes.
+ * Row-length bins in effect (sph_config.pair_bins, or the autotuner's
  * choice): the list-word target per lane of the density and of the momentum
  * sum, 0 where that sum runs with uniform lanes per particle. */
 sph_status sph_get_pair_bins(sph_ctx* ctx, int32_t* words_density, int32_t* words_momentum);
 
-/* The pair mode in effect: SPH_PAIRS_LISTS or SPH_PAIRS_FUSED (SPH_PAIRS_AUTO
+/* No paper counterpart (a choice of this library's design).
+ * The pair mode in effect: SPH_PAIRS_LISTS or SPH_PAIRS_FUSED (SPH_PAIRS_AUTO
  * resolves to one of them in sph_autotune). */
 sph_status sph_get_pair_mode(sph_ctx* ctx, int32_t* mode);
 
-/* Candidate supersets built so far (list_skin > 0: sph_find_neighbors and
+/* No paper counterpart (reused candidate supersets are this library's).
+ * Candidate supersets built so far (list_skin > 0: sph_find_neighbors and
  * the steps that had to sort and search again). */
 sph_status sph_get_list_rebuilds(sph_ctx* ctx, int64_t* n);
 
-/* Phase timers: when enabled, every phase of sph_step/sph_find_neighbors/
+/* The paper profiles its runs to find imbalance and idle time (Sec. 4.2);
+ * these are this library's timers for its own phases.
+ * Phase timers: when enabled, every phase of sph_step/sph_find_neighbors/
  * sph_density/sph_momentum_energy is bracketed by CUDA events on the
  * context's stream (graph replay is then off).  sph_get_profile returns the
  * accumulated milliseconds and launch counts per phase (SPH_PHASE_*) and
@@ -314,14 +330,16 @@ enum {
 sph_status sph_set_profiling(sph_ctx* ctx, int enable);
 sph_status sph_get_profile(sph_ctx* ctx, double* ms, int64_t* launches, int32_t nphase);
 
-/* Number of kernels this context has launched so far (graph replays count
+/* No paper counterpart (instrumentation).
+ * Number of kernels this context has launched so far (graph replays count
  * every kernel node). */
 sph_status sph_get_launch_count(sph_ctx* ctx, int64_t* launches);
 
-/* Neighbour-list size of the last sph_find_neighbors. */
+/* Neighbour-list size of the last sph_find_neighbors (Table 1's discovery). */
 sph_status sph_get_nnz(sph_ctx* ctx, int64_t* nnz);
 
-/* Sum of |N(i)| over all particles and all sph_step steps since the last
+/* No paper counterpart (instrumentation: the benchmark's pair count).
+ * Sum of |N(i)| over all particles and all sph_step steps since the last
  * reset (the pair-interaction count of the steps); reset != 0 zeroes it. */
 sph_status sph_get_pair_count(sph_ctx* ctx, int64_t* total, int reset);
 
