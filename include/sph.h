@@ -135,7 +135,7 @@ typedef struct {
     int32_t max_patches;    /* capacity of independent patches, <= 256 */
     int32_t use_graph;      /* 1: sph_step replays a captured CUDA graph */
     int32_t pair_bins;      /* load balance of the pair sums over lists of
-                               uneven length (the imbalance Sec. 4.2 finds
+                               uneven length (the imbalance Sec. 4.1 finds
                                across ranks, here across the lanes of a
                                warp): the particles are binned by row-length
                                octave after each search and each octave is
@@ -292,7 +292,7 @@ sph_status sph_get_tuning(sph_ctx* ctx, int32_t* threads_per_particle, double* c
  * momentum sum's). */
 sph_status sph_get_density_tpp(sph_ctx* ctx, int32_t* threads_per_particle);
 
-/* The load-balance settings for the imbalance Sec. 4.2 describes.
+/* The load-balance settings for the imbalance Sec. 4.1 describes.
  * Row-length bins in effect (sph_config.pair_bins, or the autotuner's
  * choice): the list-word target per lane of the density and of the momentum
  * sum, 0 where that sum runs with uniform lanes per particle. */
@@ -308,7 +308,7 @@ sph_status sph_get_pair_mode(sph_ctx* ctx, int32_t* mode);
  * the steps that had to sort and search again). */
 sph_status sph_get_list_rebuilds(sph_ctx* ctx, int64_t* n);
 
-/* The paper profiles its runs to find imbalance and idle time (Sec. 4.2);
+/* The paper profiles its runs to find imbalance and idle time (Sec. 4.1);
  * these are this library's timers for its own phases.
  * Phase timers: when enabled, every phase of sph_step/sph_find_neighbors/
  * sph_density/sph_momentum_energy is bracketed by CUDA events on the

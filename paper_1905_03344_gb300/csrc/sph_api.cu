@@ -3,6 +3,7 @@
 // checkpoints and the launch autotuner.  All device work is issued on the
 // context's stream; the kernels live in sph_sort.cu, sph_neighbors.cu,
 // sph_pairs.cu and sph_step.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -85,6 +86,7 @@ struct sph_ctx {
     bool poisoned = false;
 
     int64_t cap_n = 0, max_pairs = 0, pool_cap = 0, cap_cells = 0;
+    int64_t cells_used = 0;        // cell-table records the patches' slices span
     int cap_patch = 0, cap_items = 0;
     int64_t n = 0;
     int npatch = 0, nitems = 0, radix_passes = 3;
@@ -404,7 +406,7 @@ void enqueue_sort(sph_ctx* ctx, bool superset = false)
     }
     {
         Phase p(ctx, SPH_PHASE_GATHER);
-        cudaMemsetAsync(ctx->grid.cell, 0, (size_t)ctx->cap_cells * sizeof(uint4), ctx->stream);
+        cudaMemsetAsync(ctx->grid.cell, 0, (size_t)ctx->cells_used * sizeof(uint4), ctx->stream);
         const int nxt = 1 - ctx->cur;
         ctx->launches += launch_gather(L, ctx->n, ctx->keys, ctx->vals, ctx->st[ctx->cur], ctx->st[nxt],
                                        ctx->perm[ctx->cur], ctx->perm[nxt], ctx->pd, ctx->grid, ctx->rec,
@@ -642,8 +644,13 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
         P.item_end = (int)items.size();
         pd[p] = P;
     }
+    // the same patch layout as the current one (a state or particle set
+    // uploaded again): the work tables on the device still hold it
+    const bool same = ctx->npatch == np && (int64_t)ctx->patch_off.size() == (int64_t)np + 1 &&
+                      std::equal(offsets, offsets + np + 1, ctx->patch_off.begin()) &&
+                      ctx->nitems == (int)items.size();
     std::vector<WorkItem> units;
-    for (int p = 0; p < np; p++) {
+    for (int p = 0; p < np && !same; p++) {
         for (int64_t b = offsets[p]; b < offsets[p + 1]; b += 32) {
             WorkItem w;
             w.begin = b;
@@ -655,17 +662,20 @@ sph_status setup_patches(sph_ctx* ctx, int np, const int64_t* offsets)
     }
     if (cbase > ctx->cap_cells || (int)items.size() > ctx->cap_items || (int64_t)units.size() > ctx->cap_units)
         return fail(ctx, SPH_EINVAL, "patch table exceeds capacity");
-    if (!units.empty())
-        CK(cudaMemcpyAsync(ctx->units, units.data(), sizeof(WorkItem) * units.size(), cudaMemcpyHostToDevice,
-                           ctx->stream));
-    ctx->nunits = (int64_t)units.size();
+    if (!same) {
+        if (!units.empty())
+            CK(cudaMemcpyAsync(ctx->units, units.data(), sizeof(WorkItem) * units.size(), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        ctx->nunits = (int64_t)units.size();
+    }
     CK(cudaMemcpyAsync(ctx->pd, pd.data(), sizeof(PatchDev) * np, cudaMemcpyHostToDevice, ctx->stream));
-    if (!items.empty())
+    if (!items.empty() && !same)
         CK(cudaMemcpyAsync(ctx->items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
                            ctx->stream));
     ctx->npatch = np;
     ctx->nitems = (int)items.size();
-    if (ctx->nitems > 0) {
+    ctx->cells_used = cbase;
+    if (ctx->nitems > 0 && !same) {
         const int grid = ctx->nitems < ctx->sms * 8 ? ctx->nitems : ctx->sms * 8;
         k_fill_patch_of<<<grid, 256, 0, ctx->stream>>>(ctx->items, ctx->nitems, ctx->patch_of);
     }

@@ -92,18 +92,31 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
 {
     const int kn = a.kernel_n;
     const PairSrc src = pair_src(a);
+    // the next iteration's four row words are loaded before this
+    // iteration's pairs are summed, so that their latency overlaps the
+    // record gathers and the arithmetic (the sum order is unchanged)
+    uint32_t cw[4] = {0u, 0u, 0u, 0u};
+    if ((uint32_t)gl < len) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) cw[u] = __ldcs(row + min((uint32_t)gl + (uint32_t)(u * TPP), len - 1u));
+    }
     for (uint32_t k = gl; k < len; k += 4 * TPP) {
-        uint32_t cw[4];
         float4 q[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) cw[u] = __ldcs(row + min(k + (uint32_t)(u * TPP), len - 1u));
-#pragma unroll
         for (int u = 0; u < 4; u++) q[u] = src.r5[cw[u] & kColMask];
+        uint32_t cn[4] = {0u, 0u, 0u, 0u};
+        const uint32_t kx = k + 4u * TPP;
+        if (kx < len) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) cn[u] = __ldcs(row + min(kx + (uint32_t)(u * TPP), len - 1u));
+        }
         // (the loads past the row end repeat its last word; they are not summed)
 #pragma unroll
         for (int u = 0; u < 4; u++)
             if (k + (uint32_t)(u * TPP) < len)
                 density_pair<ZW, KERN, GH>(src, tab, I, inv2h, kn, cw[u], q[u], q[u].w, sum, comp, sumd, compd);
+#pragma unroll
+        for (int u = 0; u < 4; u++) cw[u] = cn[u];
     }
 }
 
