@@ -154,23 +154,51 @@ def sph_destroy(ctx):
     lib().sph_destroy(ctx)
 
 
+def _f64_buffer(a, n, what, exact=True):
+    """Checks that a (a torch tensor or numpy array) is a contiguous float64
+    buffer of n elements (at least n when exact is False), on the current
+    device if it is a CUDA tensor; returns (pointer, on_device).  Nothing is
+    passed to the library before these checks: a wrong dtype or length would
+    let it read or write past the buffer."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64:
+            raise ValueError("%s must be float64, not %s" % (what, a.dtype))
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+        size = a.numel()
+        if a.is_cuda and a.device.index != torch.cuda.current_device():
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d"
+                             % (what, a.device.index, torch.cuda.current_device()))
+    else:
+        if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("%s must be a contiguous float64 array" % what)
+        size = a.size
+    if (size != n) if exact else (size < n):
+        raise ValueError("%s has %d elements, %s %d expected" % (what, size, "" if exact else "at least", n))
+    return _ptr(a)
+
+
 def sph_set_particles(ctx, fields):
     """fields: dict with x y z vx vy vz m h u, each float64 of length n (all
-    torch CUDA tensors, or all numpy arrays)."""
+    torch CUDA tensors on the current device, all host tensors, or array-likes
+    converted to float64 numpy arrays)."""
     names = ["x", "y", "z", "vx", "vy", "vz", "m", "h", "u"]
-    arrs = [fields[k] for k in names]
+    missing = [k for k in names if k not in fields]
+    if missing:
+        raise ValueError("sph_set_particles: missing fields %s" % missing)
+    arrs = [fields[k] if hasattr(fields[k], "data_ptr") else np.ascontiguousarray(fields[k], dtype=np.float64)
+            for k in names]
     n = len(arrs[0])
     ptrs = []
     dev = None
-    for a in arrs:
-        if not hasattr(a, "data_ptr"):
-            a = np.ascontiguousarray(a, dtype=np.float64)
-        p, d = _ptr(a)
+    for k, a in zip(names, arrs):
+        p, d = _f64_buffer(a, n, "sph_set_particles: " + k)
         dev = d if dev is None else dev
-        if d != dev or len(a) != n:
-            raise ValueError("fields must all be device tensors or all host arrays, of equal length")
-        ptrs.append((p, a))
-    _check(ctx, lib().sph_set_particles(ctx, n, *[p for p, _ in ptrs], dev))
+        if d != dev:
+            raise ValueError("sph_set_particles: fields must all be device tensors or all host buffers")
+        ptrs.append(p)
+    _check(ctx, lib().sph_set_particles(ctx, n, *ptrs, dev))
 
 
 def sph_set_patches(ctx, offsets):
@@ -245,7 +273,7 @@ def sph_get_field(ctx, field, n, out=None):
     returns a new numpy array."""
     f = FIELD[field] if isinstance(field, str) else int(field)
     if out is not None:
-        p, d = _ptr(out)
+        p, d = _f64_buffer(out, n, "sph_get_field: out", exact=False)
         _check(ctx, lib().sph_get_field(ctx, f, p, d))
         return out
     res = np.zeros(max(n, 1))
