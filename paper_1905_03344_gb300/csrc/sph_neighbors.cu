@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
 {
     extern __shared__ __align__(16) uint32_t nb_ring[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* ring = nb_ring + warp * (32 * kRing) + lane;
+    uint32_t* ring = nb_ring + warp * (32 * (kRing + kPend)) + lane;
     if (*a.status & kStBad) return;
     const unsigned long long pool_cap = (unsigned long long)a.pool_cap;
     for (int64_t q = (int64_t)blockIdx.x * kNbtWarps + warp; q < a.nunits; q += (int64_t)gridDim.x * kNbtWarps) {
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
             const uint32_t hint = a.rowcap[i];
             if (hint == kNoHint) {
                 const RowSink<kWalkFlat, EXACT> rc =
-                    walk_all_flat<K, EXACT>(a, P, i, big, RowSink<kWalkFlat, EXACT>{nullptr, nullptr, 0u, 0u, 0u});
+                    walk_all_flat<K, EXACT>(a, P, i, big, RowSink<kWalkFlat, EXACT>{nullptr, nullptr, 0u, 0u, 0u, 0u});
                 res = round8(rc.cnt);
             } else {
                 const uint32_t c = min(hint, (uint32_t)a.n);
@@ -78,17 +78,22 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         const bool ok = base + tot <= pool_cap;
         if (!ok && lane == 0) atomicOr(a.status, kStOverflow);
         unsigned long long r0 = base + (inc - res);
-        RowSink<kWalkRing, EXACT> row = {a.col + r0, ring, ok ? res : 0u, 0u, 0u};
+        RowSink<kWalkRing, EXACT> row = {a.col + r0, ring, ok ? res : 0u, 0u, 0u, 0u};
         if (act) {
             walk_all<RowSink<kWalkRing, EXACT>, K>(a, P, i, big, row);
             row.finish();
+            if (row.npend > 0 && row.npend <= (uint32_t)kPend && row.cnt <= res) row.resolve_band(a, P, i);
         }
-        if (act && ok && row.cnt > res) {
-            // outgrew the reservation: walk again into an exact one
+        if (act && ok && (row.cnt > res || row.npend > (uint32_t)kPend)) {
+            // outgrew the reservation, or deferred more guard-band words than
+            // it notes: walk again, deciding in place, into an exact reservation
             const uint32_t need = round8(row.cnt);
             r0 = atomicAdd(&a.pool_used[0], (unsigned long long)need);
             if (r0 + need <= pool_cap) {
-                walk_all_flat<K, EXACT>(a, P, i, big, RowSink<kWalkFlat, EXACT>{a.col + r0, nullptr, need, 0u, 0u});
+                const RowSink<kWalkFlat, EXACT> rr = walk_all_flat<K, EXACT>(
+                    a, P, i, big, RowSink<kWalkFlat, EXACT>{a.col + r0, nullptr, need, 0u, 0u, 0u});
+                row.cnt = rr.cnt;
+                row.own = rr.own;
             } else {
                 atomicOr(a.status, kStOverflow);
             }
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
 template <int K, bool EXACT>
 void launch_nb_thread(const Launch& L, const NbArgs& a)
 {
-    const size_t smem = sizeof(uint32_t) * 32 * kRing * kNbtWarps;
+    const size_t smem = sizeof(uint32_t) * 32 * (kRing + kPend) * kNbtWarps;
     static int per_sm = 0;
     if (!per_sm) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nb_thread<K, EXACT>, 32 * kNbtWarps, smem);

@@ -65,6 +65,7 @@ constexpr int kGroup = SPH_NB_GROUP;
 // slots) takes a group and three pairs left over, so groups stop at 5
 static_assert(kGroup >= 1 && kGroup <= 5, "a group must fit the list ring and the pair queue");
 constexpr int kRing = 16;               // ring slots per lane (two halves of 8)
+constexpr int kPend = 4;                // guard-band words a ring row defers (per lane)
 constexpr uint32_t kHintMargin = 8;     // growth a row may have since the hint, beyond c/3
 
 // Guard band for candidates shifted by up to D cells: the FP32 error of r^2
@@ -107,14 +108,26 @@ __device__ __forceinline__ uint32_t round8(uint32_t v) { return (v + 7u) & ~7u; 
 // lane re-reads, out of L2.
 //
 // the row being built by one lane; EXACT = false: every candidate that passed
-// the coarse FP32 test (the candidate superset of reused lists), no n_i
+// the coarse FP32 test (the candidate superset of reused lists), no n_i.
+//
+// In ring mode the exact FP64 predicate is not evaluated inside the walk: a
+// candidate in the guard band is written to the row like a hit and its
+// position noted (up to kPend per row, in the lane's slots after its ring),
+// and resolve_band() decides those after the walk, removing the ones that
+// are no neighbours and counting n_i for the others.  The row is the same as
+// with the decision taken in place; the walk's inner loop only holds no call.
+// A row with more than kPend such words is walked again with the decisions
+// in place (flat mode), as a row that outgrew its reservation is.
 template <int MODE, bool EXACT = true>
 struct RowSink {
+    static constexpr bool kDefer = MODE == kWalkRing && EXACT;
     uint32_t* col;      // the row's first pool entry; flat mode: nullptr = count only
-    uint32_t* ring;     // this lane's ring (ring mode): slot k at ring[32 k]
+    uint32_t* ring;     // this lane's ring (ring mode): slot k at ring[32 k], then
+                        // kPend slots of deferred positions at ring[32 (kRing + k)]
     uint32_t res;       // entries reserved (ring mode)
     uint32_t cnt;       // entries so far
-    uint32_t own;       // n_i so far
+    uint32_t own;       // n_i so far (without the deferred words)
+    uint32_t npend;     // guard-band words deferred (ring mode)
 
     __device__ __forceinline__ void put(uint32_t w)
     {
@@ -150,9 +163,40 @@ struct RowSink {
             put(w);
             return;
         }
+        if (kDefer) {
+            const bool in = r2 < T * flo;
+            const bool io = r2 < Ti * flo;
+            if (!in || (!io && r2 <= Ti * fhi)) {
+                // guard band: kept for now, decided by resolve_band()
+                if (npend < (uint32_t)kPend) ring[32 * (kRing + npend)] = cnt;
+                npend++;
+                put(w);
+                return;
+            }
+            own += (uint32_t)io;
+            if (in) put(w);
+            return;
+        }
         const int d = pair_decision(a, P, i, j, r2, Ti, T, flo, fhi);
         own += (uint32_t)(d >> 1);
         if (d & 1) put(w);
+    }
+    // after the walk and finish(), with every word in the pool and at most
+    // kPend deferred: the exact predicate for each deferred word, last first,
+    // so that removing one leaves the positions of the earlier ones valid
+    __device__ __forceinline__ void resolve_band(const NbArgs& a, const PatchDev* P, int64_t i)
+    {
+        for (int k = (int)npend - 1; k >= 0; k--) {
+            const uint32_t pos = ring[32 * (kRing + k)];
+            const uint32_t j = col[pos] & kColMask;
+            const int e = exact_pair_at(a, i, j, P->lz);
+            own += (uint32_t)((e >> 1) & 1);
+            if (!(e & 1)) {
+                for (uint32_t m = pos; m + 1 < cnt; m++) col[m] = col[m + 1];
+                cnt--;
+            }
+        }
+        npend = 0;
     }
 };
 
