@@ -552,8 +552,15 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
             R.load(2 * hh, cwa, qa, va, ta);
             R.load(hb ? 2 * hh + 1 : 2 * hh, cwb, qb, vb, tb);
             float dxa, dya, dza, dxb, dyb, dzb;
-            col_dx<ZW>(src, tab, I, cwa, qa, dxa, dya, dza);
-            col_dx<ZW>(src, tab, I, cwb, qb, dxb, dyb, dzb);
+            // both words within the stencil (all but the few pairs with a big
+            // particle): the offset table without the per-pair branch
+            if (((cwa >> kColBits) != kFarCode) & ((cwb >> kColBits) != kFarCode)) {
+                rel_dx<ZW>(tab[cwa >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, qa, dxa, dya, dza);
+                rel_dx<ZW>(tab[cwb >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, qb, dxb, dyb, dzb);
+            } else {
+                col_dx<ZW>(src, tab, I, cwa, qa, dxa, dya, dza);
+                col_dx<ZW>(src, tab, I, cwb, qb, dxb, dyb, dzb);
+            }
             const PairTerms2 t = momentum_pair2(make_float2(dxa, dxb), make_float2(dya, dyb), make_float2(dza, dzb),
                                                 vi, ti, wi5, va, vb, ta, tb, make_float2(qa.w, hb ? qb.w : 0.0f), K);
             px = add2(px, t.ax);
