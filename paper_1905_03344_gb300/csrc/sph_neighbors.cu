@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_NB_MINB) k_nb_thread(NbArg
         if (act) {
             walk_all<RowSink<kWalkRing, EXACT>, K>(a, P, i, big, row);
             row.finish();
-            if (row.npend > 0 && row.npend <= (uint32_t)kPend && row.cnt <= res) row.resolve_band(a, P, i);
+            // only a row that is in the pool (within the sink's reservation,
+            // which is 0 for a warp whose reservation did not fit)
+            if (row.npend > 0 && row.npend <= (uint32_t)kPend && row.cnt <= row.res) row.resolve_band(a, P, i);
         }
         if (act && ok && (row.cnt > res || row.npend > (uint32_t)kPend)) {
             // outgrew the reservation, or deferred more guard-band words than
@@ -195,8 +197,8 @@ __global__ void __launch_bounds__(256) k_nb_filter(NbArgs a, const uint32_t* col
                 int D;
                 if (code != kFarCode) {
                     const float4 e = tab[code];
-                    if (zmode) rel_dx<1>(e, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
-                    else rel_dx<0>(e, s_f, sz_f, lz_f, ri.x, ri.y, ri.z, q, dx, dy, dz);
+                    if (zmode) rel_dx<1>(e, s_f, sz_f, lz_f, (float)P->ncz, ri.x, ri.y, ri.z, q, dx, dy, dz);
+                    else rel_dx<0>(e, s_f, sz_f, lz_f, (float)P->ncz, ri.x, ri.y, ri.z, q, dx, dy, dz);
                     D = Dcode;
                 } else {
                     const uint32_t cj = a.g.cellxyz[j];

@@ -93,15 +93,23 @@ __device__ __forceinline__ void rel_dx_far(uint32_t ci, uint32_t cj, float s_f, 
 }
 
 // pair separation x_i - x_j from cell-relative FP32 coordinates; ZW = 1 when
-// the patch has fewer than 2K+1 z cells (z offset as a cell count, then the
-// minimum image), ZW = 0 otherwise (signed z offset, no wrap needed)
+// the patch has fewer than 2K+1 z cells (z offset as a cell count modulo the
+// ncz cells of the period, then the minimum image), ZW = 0 otherwise (signed z
+// offset, no wrap needed).  With ZW the cell count is first taken to its
+// representative in [-ncz/2, ncz/2] (the half-period tie by the sign of the
+// offset difference), so that (j, i) takes exactly the negated shift of
+// (i, j): every step below is then symmetric under negation and the two
+// separations are exact negatives, as they are without ZW.
 template <int ZW>
-__device__ __forceinline__ void rel_dx(const float4& e, float s_f, float sz_f, float lz_f, float oxi,
+__device__ __forceinline__ void rel_dx(const float4& e, float s_f, float sz_f, float lz_f, float ncz_f, float oxi,
                                        float oyi, float ozi, const float4& q, float& dx, float& dy, float& dz)
 {
     dx = fmaf(-e.x, s_f, oxi - q.x);
     dy = fmaf(-e.y, s_f, oyi - q.y);
-    dz = fmaf(-(ZW ? e.w : e.z), sz_f, ozi - q.z);
+    const float d = ozi - q.z;
+    float k = ZW ? e.w : e.z;
+    if (ZW && (2.0f * k > ncz_f || (2.0f * k == ncz_f && d < 0.0f))) k -= ncz_f;
+    dz = fmaf(-k, sz_f, d);
     if (ZW) {
         if (dz > 0.5f * lz_f) dz -= lz_f;
         else if (dz < -0.5f * lz_f) dz += lz_f;
@@ -329,19 +337,24 @@ __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz,
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
     float F, fi = 0.0f, fj = 0.0f;
+    // F is the sum of the two sides' factors, each evaluated in the same form
+    // and added without contraction, so that it has the same bits for
+    // (i, j) and (j, i): the pair's force terms on i and on j are then exact
+    // negatives (for equal masses), and the sums conserve momentum to the
+    // rounding of the row sums alone
     if (GH) {
         const float wj2 = vj.w * vj.w;
         fi = KernF<KERN>::grad(r, vi.w, wi5, kn);
         fj = KernF<KERN>::grad(r, vj.w, wj2 * wj2 * vj.w, kn);
-        F = fi + fj;
+        F = __fadd_rn(fi, fj);
     } else if (KERN == SPH_KERNEL_WENDLAND) {
-        const float qi = fmaxf(fmaf(-r, vi.w, 1.0f), 0.0f);
-        const float wj2 = vj.w * vj.w;
+        const float wi2 = vi.w * vi.w, wj2 = vj.w * vj.w;
+        const float ai = fmaxf(fmaf(-r, wi2, vi.w), 0.0f);      // w_i q_i
         const float aj = fmaxf(fmaf(-r, wj2, vj.w), 0.0f);      // w_j q_j
-        F = fmaf(wi5, qi * qi * qi, wj2 * (aj * aj * aj));
+        F = __fadd_rn(__fmul_rn(wi2, ai * ai * ai), __fmul_rn(wj2, aj * aj * aj));
     } else {
         const float wj2 = vj.w * vj.w;
-        F = KernF<KERN>::grad(r, vi.w, wi5, kn) + KernF<KERN>::grad(r, vj.w, wj2 * wj2 * vj.w, kn);
+        F = __fadd_rn(KernF<KERN>::grad(r, vi.w, wi5, kn), KernF<KERN>::grad(r, vj.w, wj2 * wj2 * vj.w, kn));
     }
     const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const float vdot = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
@@ -353,7 +366,8 @@ __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz,
     PairTerms t;
     if (GH) {
         const float pi_f = pi_ * F;
-        const float fa = mj * fmaf(2.0f * ti.y, fi, fmaf(2.0f * tj.y, fj, pi_f));
+        // (2 A_i f_i + 2 A_j f_j) + Pi F: symmetric in i and j, as F is
+        const float fa = mj * __fadd_rn(__fadd_rn(__fmul_rn(2.0f * ti.y, fi), __fmul_rn(2.0f * tj.y, fj)), pi_f);
         t.ax = fa * dx;
         t.ay = fa * dy;
         t.az = fa * dz;
@@ -372,6 +386,14 @@ __device__ __forceinline__ PairTerms momentum_pair(float dx, float dy, float dz,
 struct MomAcc {
     float sx, cx, sy, cy, sz, cz, su, cu;
 };
+
+__device__ __forceinline__ void mom_acc_add(MomAcc& A, float bx, float by, float bz, float bu)
+{
+    kahan_add(A.sx, A.cx, bx);
+    kahan_add(A.sy, A.cy, by);
+    kahan_add(A.sz, A.cz, bz);
+    kahan_add(A.su, A.cu, bu);
+}
 
 // packed FP32x2 helpers (one instruction for both halves)
 __device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
@@ -396,13 +418,16 @@ __device__ __forceinline__ PairTerms2 momentum_pair2(float2 dx, float2 dy, float
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     const float2 r2e = add2(r2, p2(1e-30f));
     const float2 r = mul2(r2, make_float2(rsqrtf(r2e.x), rsqrtf(r2e.y)));
-    const float2 qi0 = fma2(r, p2(-vi.w), p2(1.0f));
-    const float2 qi = make_float2(fmaxf(qi0.x, 0.0f), fmaxf(qi0.y, 0.0f));
+    // both sides' factors w^2 (w q)^3 in the same form (F has the same bits
+    // for (i, j) and (j, i), as in momentum_pair)
+    const float wi2 = vi.w * vi.w;
+    const float2 ai0 = fma2(r, p2(-wi2), p2(vi.w));
+    const float2 ai = make_float2(fmaxf(ai0.x, 0.0f), fmaxf(ai0.y, 0.0f));
     const float2 wj = make_float2(va.w, vb.w);
     const float2 wj2 = mul2(wj, wj);
     const float2 aj0 = fma2(r, mul2(wj2, p2(-1.0f)), wj);
     const float2 aj = make_float2(fmaxf(aj0.x, 0.0f), fmaxf(aj0.y, 0.0f));
-    const float2 F = fma2(p2(wi5), mul2(mul2(qi, qi), qi), mul2(wj2, mul2(mul2(aj, aj), aj)));
+    const float2 F = add2(mul2(p2(wi2), mul2(mul2(ai, ai), ai)), mul2(wj2, mul2(mul2(aj, aj), aj)));
     const float2 vx = sub2(p2(vi.x), make_float2(va.x, vb.x));
     const float2 vy = sub2(p2(vi.y), make_float2(va.y, vb.y));
     const float2 vz = sub2(p2(vi.z), make_float2(va.z, vb.z));
@@ -447,11 +472,12 @@ struct PairSide {
     float4 ri;                 // r5 of i
     uint32_t ci;               // cell of i
     float s_f, sz_f, lz_f;     // cell edges and z period of i's patch
+    float ncz_f;               // z cells of the period
 };
 
 __device__ __forceinline__ PairSide pair_side(const PairArgs& a, const PatchDev* P, int64_t i)
 {
-    return PairSide{a.r.r5[i], a.cellxyz[i], P->s_f, P->sz_f, P->lz_f};
+    return PairSide{a.r.r5[i], a.cellxyz[i], P->s_f, P->sz_f, P->lz_f, (float)P->ncz};
 }
 
 // x_i - x_j for column word cw, q = r5 of j
@@ -461,19 +487,17 @@ __device__ __forceinline__ void col_dx(const PairSrc& src, const float4* tab, co
 {
     const uint32_t code = cw >> kColBits;
     if (code != kFarCode)
-        rel_dx<ZW>(tab[code], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, q, dx, dy, dz);
+        rel_dx<ZW>(tab[code], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, q, dx, dy, dz);
     else
         rel_dx_far(I.ci, src.cellxyz[cw & kColMask], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, q, dx, dy, dz);
 }
 
-// density: one Kahan step of m W-shape(r) (and of m (-v S'(v)) for grad-h)
-template <int ZW, int KERN, bool GH>
-__device__ __forceinline__ void density_pair(const PairSrc& src, const float4* tab, const PairSide& I, float inv2h,
-                                             int kn, uint32_t cw, const float4& q, float m, float& sum, float& comp,
-                                             float& sumd, float& compd)
+// density: one Kahan step of m W-shape(r) (and of m (-v S'(v)) for grad-h),
+// from x_i - x_j = (dx, dy, dz)
+template <int KERN, bool GH>
+__device__ __forceinline__ void density_term(float dx, float dy, float dz, float inv2h, int kn, float m, float& sum,
+                                             float& comp, float& sumd, float& compd)
 {
-    float dx, dy, dz;
-    col_dx<ZW>(src, tab, I, cw, q, dx, dy, dz);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float r = r2 * rsqrtf(r2 + 1e-30f);
     if (GH) {
@@ -484,6 +508,17 @@ __device__ __forceinline__ void density_pair(const PairSrc& src, const float4* t
     } else {
         kahan_fma(sum, comp, m, KernF<KERN>::dens(r, inv2h, kn));
     }
+}
+
+// the same for column word cw, q = r5 of j
+template <int ZW, int KERN, bool GH>
+__device__ __forceinline__ void density_pair(const PairSrc& src, const float4* tab, const PairSide& I, float inv2h,
+                                             int kn, uint32_t cw, const float4& q, float m, float& sum, float& comp,
+                                             float& sumd, float& compd)
+{
+    float dx, dy, dz;
+    col_dx<ZW>(src, tab, I, cw, q, dx, dy, dz);
+    density_term<KERN, GH>(dx, dy, dz, inv2h, kn, m, sum, comp, sumd, compd);
 }
 
 // density epilogue of particle i: rho from the shape sum (self term m_i),
@@ -555,8 +590,8 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
             // both words within the stencil (all but the few pairs with a big
             // particle): the offset table without the per-pair branch
             if (((cwa >> kColBits) != kFarCode) & ((cwb >> kColBits) != kFarCode)) {
-                rel_dx<ZW>(tab[cwa >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, qa, dxa, dya, dza);
-                rel_dx<ZW>(tab[cwb >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, qb, dxb, dyb, dzb);
+                rel_dx<ZW>(tab[cwa >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, qa, dxa, dya, dza);
+                rel_dx<ZW>(tab[cwb >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, qb, dxb, dyb, dzb);
             } else {
                 col_dx<ZW>(src, tab, I, cwa, qa, dxa, dya, dza);
                 col_dx<ZW>(src, tab, I, cwb, qb, dxb, dyb, dzb);
@@ -588,14 +623,6 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
             bu += t.du;
         }
     }
-}
-
-__device__ __forceinline__ void mom_acc_add(MomAcc& A, float bx, float by, float bz, float bu)
-{
-    kahan_add(A.sx, A.cx, bx);
-    kahan_add(A.sy, A.cy, by);
-    kahan_add(A.sz, A.cz, bz);
-    kahan_add(A.su, A.cu, bu);
 }
 
 // momentum epilogue of particle i

@@ -83,8 +83,12 @@ __device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowA
 // ---------------------------------------------------------------------------
 // density + EOS, mixed precision
 // ---------------------------------------------------------------------------
-// the row of one particle: plain FP32 weights m_j W-shape(r), Kahan sum, four
-// neighbours per lane and iteration (their gathers are issued together)
+// the row of one particle: plain FP32 weights m_j W-shape(r), Kahan sum.  A
+// lane takes the row in chunks of four words (one 16-byte load; rows start on
+// 32-byte boundaries and are reserved in multiples of 8 words, so a chunk
+// never leaves the reservation), loaded one chunk ahead of its use, and
+// issues the chunk's four record gathers together.  Words past the row end
+// in the last chunk are not used as indices.
 template <int TPP, int ZW, int KERN, bool GH>
 __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
                                             int gl, const PairSide& I, float inv2h, float& sum, float& comp,
@@ -92,36 +96,42 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
 {
     const int kn = a.kernel_n;
     const PairSrc src = pair_src(a);
-    // the next iteration's four row words are loaded before this
-    // iteration's pairs are summed, so that their latency overlaps the
-    // record gathers and the arithmetic (the sum order is unchanged)
-    uint32_t cw[4] = {0u, 0u, 0u, 0u};
-    if ((uint32_t)gl < len) {
-#pragma unroll
-        for (int u = 0; u < 4; u++) cw[u] = __ldcs(row + min((uint32_t)gl + (uint32_t)(u * TPP), len - 1u));
-    }
-    for (uint32_t k = gl; k < len; k += 4 * TPP) {
+    const uint4* row4 = reinterpret_cast<const uint4*>(row);
+    const uint32_t nch = (len + 3u) >> 2;
+    uint32_t ch = (uint32_t)gl;
+    uint4 w = ch < nch ? __ldcs(row4 + ch) : make_uint4(0u, 0u, 0u, 0u);
+    for (; ch < nch; ch += TPP) {
+        const uint4 wn = ch + TPP < nch ? __ldcs(row4 + ch + TPP) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t nv = min(len - ch * 4u, 4u);
+        const uint32_t cw[4] = {w.x, nv > 1u ? w.y : w.x, nv > 2u ? w.z : w.x, nv > 3u ? w.w : w.x};
         float4 q[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) q[u] = src.r5[cw[u] & kColMask];
-        uint32_t cn[4] = {0u, 0u, 0u, 0u};
-        const uint32_t kx = k + 4u * TPP;
-        if (kx < len) {
+        float dx[4], dy[4], dz[4];
+        // all four words within the stencil (all but the few pairs with a big
+        // particle): the offset table without the per-pair branch
+        if (((cw[0] >> kColBits) != kFarCode) & ((cw[1] >> kColBits) != kFarCode) &
+            ((cw[2] >> kColBits) != kFarCode) & ((cw[3] >> kColBits) != kFarCode)) {
 #pragma unroll
-            for (int u = 0; u < 4; u++) cn[u] = __ldcs(row + min(kx + (uint32_t)(u * TPP), len - 1u));
+            for (int u = 0; u < 4; u++)
+                rel_dx<ZW>(tab[cw[u] >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, q[u], dx[u],
+                           dy[u], dz[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++) col_dx<ZW>(src, tab, I, cw[u], q[u], dx[u], dy[u], dz[u]);
         }
-        // (the loads past the row end repeat its last word; they are not summed)
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            if (k + (uint32_t)(u * TPP) < len)
-                density_pair<ZW, KERN, GH>(src, tab, I, inv2h, kn, cw[u], q[u], q[u].w, sum, comp, sumd, compd);
-#pragma unroll
-        for (int u = 0; u < 4; u++) cw[u] = cn[u];
+            if ((uint32_t)u < nv) density_term<KERN, GH>(dx[u], dy[u], dz[u], inv2h, kn, q[u].w, sum, comp, sumd, compd);
+        w = wn;
     }
 }
 
+#ifndef SPH_DEN_MINB
+#define SPH_DEN_MINB 4                  // resident 256-thread CTAs per SM the registers are sized for
+#endif
 template <int TPP, int KERN, bool GH>
-__global__ void __launch_bounds__(256) k_density_mixed(PairArgs a)
+__global__ void __launch_bounds__(256, SPH_DEN_MINB) k_density_mixed(PairArgs a)
 {
     const float kb8 = (float)(8.0 * a.kb);
     __shared__ float4 tab[kStencilCells];

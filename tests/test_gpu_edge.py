@@ -107,6 +107,23 @@ def test_overflow_leaves_state(B):
     sim.close()
 
 
+def test_overflow_of_long_rows_with_guard_band_words(B):
+    """Rows of ~700 neighbours in a random cloud (many of them with words in
+    the guard band, decided after the walk) against a pool far too small:
+    the warps whose reservations do not fit must leave the pool alone, so the
+    call reports the overflow and the context stays usable."""
+    f = inputs.random_cloud(20000, seed=3)
+    n = len(f["x"])
+    sim = B.SPH(n, precision="fp64", max_pairs=10 * n)
+    sim.set_particles(f)
+    for _ in range(2):
+        with pytest.raises(B.SphError) as e:
+            sim.find_neighbors()
+        assert e.value.status == B.SPH_EOVERFLOW
+    assert np.array_equal(sim.field("x"), f["x"])
+    sim.close()
+
+
 def test_bad_inputs(B):
     sim = B.SPH(8)
     f = _fields(3)
