@@ -52,7 +52,6 @@ __device__ __forceinline__ bool union_decision(const NbArgs& a, const PatchDev* 
 template <int KERN, bool GH>
 struct DensSink {
     PairSrc src;
-    const float4* tab;
     PairSide I;
     float inv2h;
     int kn, zmode;
@@ -69,15 +68,14 @@ struct DensSink {
         if (!(d & 1)) return;
         cnt++;
         const float4 q = src.r5[j];
-        if (zmode) density_pair<1, KERN, GH>(src, tab, I, inv2h, kn, w, q, q.w, sum, comp, sumd, compd);
-        else density_pair<0, KERN, GH>(src, tab, I, inv2h, kn, w, q, q.w, sum, comp, sumd, compd);
+        if (zmode) density_pair<1, KERN, GH>(src, I, inv2h, kn, w, q, q.w, sum, comp, sumd, compd);
+        else density_pair<0, KERN, GH>(src, I, inv2h, kn, w, q, q.w, sum, comp, sumd, compd);
     }
 };
 
 template <int KERN, bool GH>
 struct MomSink {
     PairSrc src;
-    const float4* tab;
     PairSide I;
     float4 vi, ti;
     float wi5;
@@ -102,8 +100,8 @@ struct MomSink {
                                  q[32 * ((head + 2) & (kQueue - 1))], q[32 * ((head + 3) & (kQueue - 1))]};
         float bx, by, bz, bu;
         const GlobalRecs R{src};
-        if (zmode) momentum_chunk<1, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, R);
-        else momentum_chunk<0, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, R);
+        if (zmode) momentum_chunk<1, KERN, GH>(src, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, R);
+        else momentum_chunk<0, KERN, GH>(src, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, R);
         mom_acc_add(A, bx, by, bz, bu);
         head += nv;
     }
@@ -191,8 +189,6 @@ template <int K, int KERN, bool GH>
 __global__ void __launch_bounds__(32 * kNbtWarps, SPH_FUSED_DEN_MINB)
     k_fused_density_mixed(NbArgs a, const __grid_constant__ PairArgs pa)
 {
-    __shared__ float4 tab[kStencilCells];
-    fill_stencil_table(tab);
     if (*a.status & kStBad) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float kb8 = (float)(8.0 * pa.kb), gam = (float)pa.gamma;
@@ -204,7 +200,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_FUSED_DEN_MINB)
         uint32_t cnt = 0;
         if (i < U.end) {
             const bool big = i >= P->end - (int64_t)P->nbig;
-            DensSink<KERN, GH> s = {src, tab, pair_side(pa, P, i), pa.r.rv[i].w, pa.kernel_n, P->zmode,
+            DensSink<KERN, GH> s = {src, pair_side(pa, P, i), pa.r.rv[i].w, pa.kernel_n, P->zmode,
                                     0.0f, 0.0f, 0.0f, 0.0f, 0u, 0u};
             walk_all<DensSink<KERN, GH>, K>(a, P, i, big, s);
             density_finish<GH>(pa, i, s.I.ri.w, s.inv2h, kb8, gam, s.sum, s.comp, s.sumd, s.compd);
@@ -220,9 +216,7 @@ template <int K, int KERN, bool GH>
 __global__ void __launch_bounds__(32 * kNbtWarps, SPH_FUSED_MOM_MINB)
     k_fused_momentum_mixed(NbArgs a, const __grid_constant__ PairArgs pa)
 {
-    __shared__ float4 tab[kStencilCells];
     __shared__ uint32_t qbuf[kNbtWarps * 32 * kQueue];
-    fill_stencil_table(tab);
     if (*a.status & kStBad) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float gscale = (float)KernF<KERN>::grad_scale(pa.kb, pa.kernel_n);
@@ -237,7 +231,7 @@ __global__ void __launch_bounds__(32 * kNbtWarps, SPH_FUSED_MOM_MINB)
             const bool big = i >= P->end - (int64_t)P->nbig;
             const float4 vi = pa.r.rv[i];
             const float wi2 = vi.w * vi.w;
-            MomSink<KERN, GH> s = {src, tab, pair_side(pa, P, i), vi, pa.r.rt[i], wi2 * wi2 * vi.w, Kc,
+            MomSink<KERN, GH> s = {src, pair_side(pa, P, i), vi, pa.r.rt[i], wi2 * wi2 * vi.w, Kc,
                                    pa.kernel_n, P->zmode, qlane, 0u, 0u, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
             walk_all<MomSink<KERN, GH>, K>(a, P, i, big, s);
             s.finish();

@@ -164,8 +164,6 @@ int launch_nb_lists(const Launch& L, const NbArgs& a, int K, int exact)
 template <int TPP>
 __global__ void __launch_bounds__(256) k_nb_filter(NbArgs a, const uint32_t* col_s, const uint32_t* cnt_s)
 {
-    __shared__ float4 tab[kStencilCells];
-    fill_stencil_table(tab);
     if (*a.status & kStBad) return;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (TPP - 1);
@@ -196,7 +194,7 @@ __global__ void __launch_bounds__(256) k_nb_filter(NbArgs a, const uint32_t* col
                 float dx, dy, dz;
                 int D;
                 if (code != kFarCode) {
-                    const float4 e = tab[code];
+                    const float4 e = stencil_offset(code);
                     if (zmode) rel_dx<1>(e, s_f, sz_f, lz_f, (float)P->ncz, ri.x, ri.y, ri.z, q, dx, dy, dz);
                     else rel_dx<0>(e, s_f, sz_f, lz_f, (float)P->ncz, ri.x, ri.y, ri.z, q, dx, dy, dz);
                     D = Dcode;

@@ -51,15 +51,21 @@ __device__ __forceinline__ double group_sum(double v, unsigned gmask)
     return v;
 }
 
-// stencil offsets of the packed column word: {dcx, dcy, dcz, t}, the z entry
-// used with zmode 0, t (z cell offset, FP32 minimum image) with zmode 1
-__device__ __forceinline__ void fill_stencil_table(float4* tab)
+// the stencil offsets of a column word's code (< 125): {dcx, dcy, dcz, zd},
+// dcz used with zmode 0, zd (the z cell count, FP32 minimum image) with zmode
+// 1.  Integer arithmetic instead of a table (no shared-memory load per pair):
+// zd = code / 25 as (code 1311) >> 15 and r / 5 as (r 13) >> 6, both exact
+// for code < 125, and each small integer n converted as the float 2^23 + n,
+// whose bits are 0x4B000000 | n, minus 2^23 (exact)
+__device__ __forceinline__ float4 stencil_offset(uint32_t code)
 {
-    for (int k = threadIdx.x; k < kStencilCells; k += blockDim.x) {
-        const int zd = k / 25;
-        tab[k] = make_float4((float)(k % 5 - 2), (float)((k / 5) % 5 - 2), (float)(zd - 2), (float)zd);
-    }
-    __syncthreads();
+    const uint32_t zd = (code * 1311u) >> 15;
+    const uint32_t r = code - 25u * zd;
+    const uint32_t yd = (r * 13u) >> 6;
+    const uint32_t xd = r - 5u * yd;
+    const float fz = __uint_as_float(0x4B000000u | zd);
+    return make_float4(__uint_as_float(0x4B000000u | xd) - 8388610.0f, __uint_as_float(0x4B000000u | yd) - 8388610.0f,
+                       fz - 8388610.0f, fz - 8388608.0f);
 }
 
 struct GroupIdx {
@@ -482,12 +488,12 @@ __device__ __forceinline__ PairSide pair_side(const PairArgs& a, const PatchDev*
 
 // x_i - x_j for column word cw, q = r5 of j
 template <int ZW>
-__device__ __forceinline__ void col_dx(const PairSrc& src, const float4* tab, const PairSide& I, uint32_t cw,
+__device__ __forceinline__ void col_dx(const PairSrc& src, const PairSide& I, uint32_t cw,
                                        const float4& q, float& dx, float& dy, float& dz)
 {
     const uint32_t code = cw >> kColBits;
     if (code != kFarCode)
-        rel_dx<ZW>(tab[code], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, q, dx, dy, dz);
+        rel_dx<ZW>(stencil_offset(code), I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, q, dx, dy, dz);
     else
         rel_dx_far(I.ci, src.cellxyz[cw & kColMask], I.s_f, I.sz_f, I.lz_f, I.ri.x, I.ri.y, I.ri.z, q, dx, dy, dz);
 }
@@ -512,12 +518,12 @@ __device__ __forceinline__ void density_term(float dx, float dy, float dz, float
 
 // the same for column word cw, q = r5 of j
 template <int ZW, int KERN, bool GH>
-__device__ __forceinline__ void density_pair(const PairSrc& src, const float4* tab, const PairSide& I, float inv2h,
+__device__ __forceinline__ void density_pair(const PairSrc& src, const PairSide& I, float inv2h,
                                              int kn, uint32_t cw, const float4& q, float m, float& sum, float& comp,
                                              float& sumd, float& compd)
 {
     float dx, dy, dz;
-    col_dx<ZW>(src, tab, I, cw, q, dx, dy, dz);
+    col_dx<ZW>(src, I, cw, q, dx, dy, dz);
     density_term<KERN, GH>(dx, dy, dz, inv2h, kn, m, sum, comp, sumd, compd);
 }
 
@@ -567,7 +573,7 @@ struct GlobalRecs {
 // momentum: the plain sums (bx, by, bz, bu) of up to four pairs, the column
 // words cws[0 .. nv), the records of pair u from R.load(u, ...)
 template <int ZW, int KERN, bool GH, class Recs4 = GlobalRecs>
-__device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4* tab, const PairSide& I,
+__device__ __forceinline__ void momentum_chunk(const PairSrc& src, const PairSide& I,
                                                const float4& vi, const float4& ti, float wi5, const MomConst& K,
                                                int kn, const uint32_t (&cws)[4], uint32_t nv, float& bx, float& by,
                                                float& bz, float& bu, const Recs4& R)
@@ -588,13 +594,13 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
             R.load(hb ? 2 * hh + 1 : 2 * hh, cwb, qb, vb, tb);
             float dxa, dya, dza, dxb, dyb, dzb;
             // both words within the stencil (all but the few pairs with a big
-            // particle): the offset table without the per-pair branch
+            // particle): the stencil offsets without the per-pair branch
             if (((cwa >> kColBits) != kFarCode) & ((cwb >> kColBits) != kFarCode)) {
-                rel_dx<ZW>(tab[cwa >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, qa, dxa, dya, dza);
-                rel_dx<ZW>(tab[cwb >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, qb, dxb, dyb, dzb);
+                rel_dx<ZW>(stencil_offset(cwa >> kColBits), I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, qa, dxa, dya, dza);
+                rel_dx<ZW>(stencil_offset(cwb >> kColBits), I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, qb, dxb, dyb, dzb);
             } else {
-                col_dx<ZW>(src, tab, I, cwa, qa, dxa, dya, dza);
-                col_dx<ZW>(src, tab, I, cwb, qb, dxb, dyb, dzb);
+                col_dx<ZW>(src, I, cwa, qa, dxa, dya, dza);
+                col_dx<ZW>(src, I, cwb, qb, dxb, dyb, dzb);
             }
             const PairTerms2 t = momentum_pair2(make_float2(dxa, dxb), make_float2(dya, dyb), make_float2(dza, dzb),
                                                 vi, ti, wi5, va, vb, ta, tb, make_float2(qa.w, hb ? qb.w : 0.0f), K);
@@ -615,7 +621,7 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const float4*
             float4 q, vj, tj;
             R.load(u, cw, q, vj, tj);
             float dx, dy, dz;
-            col_dx<ZW>(src, tab, I, cw, q, dx, dy, dz);
+            col_dx<ZW>(src, I, cw, q, dx, dy, dz);
             const PairTerms t = momentum_pair<KERN, GH>(dx, dy, dz, vi, ti, wi5, vj, tj, q.w, K, kn);
             bx += t.ax;
             by += t.ay;

@@ -90,7 +90,7 @@ __device__ __forceinline__ void row_ahead_prefetch(const PairArgs& a, const RowA
 // issues the chunk's four record gathers together.  Words past the row end
 // in the last chunk are not used as indices.
 template <int TPP, int ZW, int KERN, bool GH>
-__device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
+__device__ __forceinline__ void density_row(const PairArgs& a, const uint32_t* row, uint32_t len,
                                             int gl, const PairSide& I, float inv2h, float& sum, float& comp,
                                             float& sumd, float& compd)
 {
@@ -109,16 +109,16 @@ __device__ __forceinline__ void density_row(const PairArgs& a, const float4* tab
         for (int u = 0; u < 4; u++) q[u] = src.r5[cw[u] & kColMask];
         float dx[4], dy[4], dz[4];
         // all four words within the stencil (all but the few pairs with a big
-        // particle): the offset table without the per-pair branch
+        // particle): the stencil offsets without the per-pair branch
         if (((cw[0] >> kColBits) != kFarCode) & ((cw[1] >> kColBits) != kFarCode) &
             ((cw[2] >> kColBits) != kFarCode) & ((cw[3] >> kColBits) != kFarCode)) {
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                rel_dx<ZW>(tab[cw[u] >> kColBits], I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, q[u], dx[u],
+                rel_dx<ZW>(stencil_offset(cw[u] >> kColBits), I.s_f, I.sz_f, I.lz_f, I.ncz_f, I.ri.x, I.ri.y, I.ri.z, q[u], dx[u],
                            dy[u], dz[u]);
         } else {
 #pragma unroll
-            for (int u = 0; u < 4; u++) col_dx<ZW>(src, tab, I, cw[u], q[u], dx[u], dy[u], dz[u]);
+            for (int u = 0; u < 4; u++) col_dx<ZW>(src, I, cw[u], q[u], dx[u], dy[u], dz[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; u++)
@@ -134,8 +134,6 @@ template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256, SPH_DEN_MINB) k_density_mixed(PairArgs a)
 {
     const float kb8 = (float)(8.0 * a.kb);
-    __shared__ float4 tab[kStencilCells];
-    fill_stencil_table(tab);
     if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
@@ -154,8 +152,8 @@ __global__ void __launch_bounds__(256, SPH_DEN_MINB) k_density_mixed(PairArgs a)
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
         float sum = 0.0f, comp = 0.0f, sumd = 0.0f, compd = 0.0f;
-        if (P->zmode) density_row<TPP, 1, KERN, GH>(a, tab, row, len, G.gl, I, inv2h, sum, comp, sumd, compd);
-        else density_row<TPP, 0, KERN, GH>(a, tab, row, len, G.gl, I, inv2h, sum, comp, sumd, compd);
+        if (P->zmode) density_row<TPP, 1, KERN, GH>(a, row, len, G.gl, I, inv2h, sum, comp, sumd, compd);
+        else density_row<TPP, 0, KERN, GH>(a, row, len, G.gl, I, inv2h, sum, comp, sumd, compd);
         group_kahan_reduce<TPP>(sum, comp, G.gmask);
         if (GH) group_kahan_reduce<TPP>(sumd, compd, G.gmask);
         if (G.gl == 0) density_finish<GH>(a, i, I.ri.w, inv2h, kb8, gam, sum, comp, sumd, compd);
@@ -200,7 +198,7 @@ __global__ void __launch_bounds__(256) k_density_fp64(PairArgs a)
 // compensation (the plain sum of four terms errs by at most 3 eps times their
 // magnitudes, the order of one term's own rounding).
 template <int TPP, int ZW, int KERN, bool GH>
-__device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* tab, const uint32_t* row, uint32_t len,
+__device__ __forceinline__ void momentum_row(const PairArgs& a, const uint32_t* row, uint32_t len,
                                              int gl, const PairSide& I, const float4& vi, const float4& ti, float wi5,
                                              const MomConst& K, MomAcc& A)
 {
@@ -215,7 +213,7 @@ __device__ __forceinline__ void momentum_row(const PairArgs& a, const float4* ta
         const uint32_t cws[4] = {w.x, w.y, w.z, w.w};
         const uint32_t nv = min(len - ch * 4u, 4u);
         float bx, by, bz, bu;
-        momentum_chunk<ZW, KERN, GH>(src, tab, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, GlobalRecs{src});
+        momentum_chunk<ZW, KERN, GH>(src, I, vi, ti, wi5, K, kn, cws, nv, bx, by, bz, bu, GlobalRecs{src});
         mom_acc_add(A, bx, by, bz, bu);
         w = wn;
     }
@@ -228,8 +226,6 @@ template <int TPP, int KERN, bool GH>
 __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a)
 {
     const float gscale = (float)KernF<KERN>::grad_scale(a.kb, a.kernel_n);
-    __shared__ float4 tab[kStencilCells];
-    fill_stencil_table(tab);
     if (*a.status & kStBad) return;
     const GroupIdx G = group_idx<TPP>();
     const int64_t gs = ((int64_t)gridDim.x * blockDim.x) / TPP;
@@ -251,8 +247,8 @@ __global__ void __launch_bounds__(256, SPH_MOM_MINB) k_momentum_mixed(PairArgs a
         const uint32_t* row = a.col + a.rowstart[i];
         const uint32_t len = a.cnt[i];
         MomAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (P->zmode) momentum_row<TPP, 1, KERN, GH>(a, tab, row, len, G.gl, I, vi, ti, wi5, K, A);
-        else momentum_row<TPP, 0, KERN, GH>(a, tab, row, len, G.gl, I, vi, ti, wi5, K, A);
+        if (P->zmode) momentum_row<TPP, 1, KERN, GH>(a, row, len, G.gl, I, vi, ti, wi5, K, A);
+        else momentum_row<TPP, 0, KERN, GH>(a, row, len, G.gl, I, vi, ti, wi5, K, A);
         group_kahan_reduce<TPP>(A.sx, A.cx, G.gmask);
         group_kahan_reduce<TPP>(A.sy, A.cy, G.gmask);
         group_kahan_reduce<TPP>(A.sz, A.cz, G.gmask);
