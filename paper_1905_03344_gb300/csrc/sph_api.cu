@@ -119,6 +119,7 @@ struct sph_ctx {
     uint32_t* perm[2] = {nullptr, nullptr};
     uint16_t* patch_of = nullptr;
     uint32_t *keys = nullptr, *vals = nullptr, *keys_alt = nullptr, *vals_alt = nullptr;
+    float* hnb_tmp = nullptr;   // one float per cell: the x-y pass of the grid's hnb
     uint32_t *hist = nullptr, *scan32 = nullptr;
     Grid grid{};
     Recs rec{};
@@ -415,6 +416,7 @@ void enqueue_sort(sph_ctx* ctx, bool superset = false)
                                                 : RowHint{ctx->cnt, ctx->hint_ok, ctx->rowcap},
                                        superset ? ctx->hsearch_pre : nullptr, superset ? ctx->skinref.h0 : nullptr);
         ctx->launches += launch_cell_boxes(L, ctx->npatch, ctx->pd, ctx->grid, ctx->rec.r4);
+        ctx->launches += launch_cell_hnb(L, ctx->npatch, ctx->pd, ctx->grid, stencil_k(ctx->cell_factor), ctx->hnb_tmp);
         ctx->cur = nxt;
     }
     ctx->fresh = false;
@@ -874,7 +876,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ok = ok && dalloc(ctx, ctx->hist, hw) && dalloc(ctx, ctx->scan32, (size_t)scan_tmp_words((int64_t)hw));
     uint4* cellrec = nullptr;
     uint32_t* cellxyz = nullptr;
-    ok = ok && dalloc(ctx, cellrec, (size_t)ctx->cap_cells) && dalloc(ctx, cellxyz, N);
+    ok = ok && dalloc(ctx, cellrec, (size_t)ctx->cap_cells) && dalloc(ctx, cellxyz, N) &&
+         dalloc(ctx, ctx->grid.hnb, (size_t)ctx->cap_cells) && dalloc(ctx, ctx->hnb_tmp, (size_t)ctx->cap_cells);
     ctx->grid.cell = cellrec;
     ctx->grid.cellxyz = cellxyz;
     // kGroup-style padding: the list search reads groups of records past a cell

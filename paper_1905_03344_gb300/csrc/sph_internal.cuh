@@ -111,6 +111,9 @@ struct Grid {
     uint4* cell;         // [cell] record above
     uint32_t* cellxyz;   // [particle] cx | cy << 8 | cz << 16
     const uint16_t* patch_of;  // [particle] patch index
+    float* hnb;          // [fine cell] the largest h of the fine cells within
+                         // K cells along each axis (z periodic): no small
+                         // particle searching from this cell meets a larger one
 };
 
 struct Recs {             // FP32 records (written by gather / density)
@@ -207,6 +210,8 @@ int launch_refresh_records(const Launch& L, int64_t n, const State& s, const uin
                            const PatchDev* pd, const uint32_t* cellxyz, const Recs& r, const Fp64& f, int mixed);
 // tight boxes of the fine cells (after the gather)
 int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4);
+// g.hnb for stencil half-extent K (tmp: one float per cell)
+int launch_cell_hnb(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, int K, float* tmp);
 // temporary words of the device-wide exclusive scan over n values
 int64_t scan_tmp_words(int64_t n);
 

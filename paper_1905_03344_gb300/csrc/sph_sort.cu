@@ -780,6 +780,55 @@ __global__ void __launch_bounds__(256) k_cell_boxes(const PatchDev* pd, Grid g, 
     }
 }
 
+// The largest h within K fine cells of each fine cell, a separable maximum:
+// over the (2K+1)^2 cells of its x-y square (in range), then over 2K+1 z
+// planes (periodic; with fewer z cells than that, every plane).  A small
+// particle's search from this cell reaches no farther than 2 max(h_i, hnb).
+__global__ void __launch_bounds__(256) k_hnb_xy(const PatchDev* pd, Grid g, int K, float* tmp)
+{
+    const PatchDev* P = pd + blockIdx.y;
+    const int ncx = P->ncx, ncy = P->ncy;
+    const int64_t nfine = (int64_t)ncx * ncy * P->ncz;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nfine; c += (int64_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % ncx), cy = (int)((c / ncx) % ncy);
+        const int64_t plane = c - (int64_t)cy * ncx - cx;
+        float m = 0.0f;
+        for (int y = max(cy - K, 0); y <= min(cy + K, ncy - 1); y++)
+            for (int x = max(cx - K, 0); x <= min(cx + K, ncx - 1); x++)
+                m = fmaxf(m, __uint_as_float(g.cell[P->cell_base + plane + (int64_t)y * ncx + x].z));
+        tmp[P->cell_base + c] = m;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_hnb_z(const PatchDev* pd, Grid g, int K, const float* tmp)
+{
+    const PatchDev* P = pd + blockIdx.y;
+    const int64_t nxy = (int64_t)P->ncx * P->ncy;
+    const int ncz = P->ncz;
+    const int64_t nfine = nxy * ncz;
+    const int kz = 2 * K + 1 > ncz ? (ncz - 1) / 2 + 1 : K;   // every plane when they are fewer
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nfine; c += (int64_t)gridDim.x * blockDim.x) {
+        const int cz = (int)(c / nxy);
+        const int64_t r = c - (int64_t)cz * nxy;
+        float m = 0.0f;
+        for (int dz = -kz; dz <= kz; dz++) {
+            int z = cz + dz;
+            z = ((z % ncz) + ncz) % ncz;
+            m = fmaxf(m, tmp[P->cell_base + (int64_t)z * nxy + r]);
+        }
+        g.hnb[P->cell_base + c] = m;
+    }
+}
+
+int launch_cell_hnb(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, int K, float* tmp)
+{
+    if (npatch <= 0) return 0;
+    const int bx = npatch > 8 ? 8 : (L.sms * 4 + npatch - 1) / npatch;
+    k_hnb_xy<<<dim3((unsigned)bx, (unsigned)npatch), 256, 0, L.stream>>>(pd, g, K, tmp);
+    k_hnb_z<<<dim3((unsigned)bx, (unsigned)npatch), 256, 0, L.stream>>>(pd, g, K, tmp);
+    return 2;
+}
+
 int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4)
 {
     if (npatch <= 0) return 0;

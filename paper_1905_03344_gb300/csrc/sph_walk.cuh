@@ -248,7 +248,9 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
     const float tol = guard_tol(s_f / hf, ZW ? max(K, ncz) : K);
     const float flo = 1.0f - tol, fhi = 1.0f + tol;
     const float slack = (1.0f / 4096.0f) * s_f;
-    const float Rg = 2.0f * fmaxf(hf, P->hs_f) * (1.0f + 1.0f / 512.0f) + slack;
+    // no small neighbour within the stencil has h above hnb of i's cell
+    const float hn = a.g.hnb[cbase + ((uint32_t)cz * (uint32_t)ncy + (uint32_t)cy) * (uint32_t)ncx + (uint32_t)cx];
+    const float Rg = 2.0f * fmaxf(hf, hn) * (1.0f + 1.0f / 512.0f) + slack;
     const float Rg2 = Rg * Rg;
     const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
     const float qs = s_f * (1.0f / kBoxQ), qsz = sz_f * (1.0f / kBoxQ);
