@@ -110,7 +110,10 @@ typedef struct {
     int32_t threads_per_particle; /* 0 = auto; else 1, 2, 4, 8, 16 or 32 */
     int32_t pair_mode;      /* SPH_PAIRS_LISTS (default), _FUSED or _AUTO */
     double cell_factor;     /* cell edge = 2 h_s * cell_factor, in [1/3, 4]
-                               (h_s: the patch's class threshold of h) */
+                               (h_s: the patch's class threshold of h);
+                               below 1/2 the stencil reaches 3 cells and the
+                               edge is at least min(h_s, 1.3 h_median).
+                               0 (default): 1/2 */
     double list_skin;       /* 0 (default): every step sorts and searches.
                                skin > 0 (at most 1; list mode only): the search
                                lists the candidate superset r < 2 (1 + skin)

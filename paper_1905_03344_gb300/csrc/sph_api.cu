@@ -1398,7 +1398,8 @@ sph_status sph_autotune(sph_ctx* ctx)
     const bool prof0 = ctx->prof;
     ctx->prof = false;
     destroy_graphs(ctx);
-    const double factors[4] = {1.0 / 3.0, 0.5, 0.75, 1.0};
+    // 1/3 and 0.4 (a 3-cell stencil) take cells down to min(h_s, 1.3 h_median)
+    const double factors[5] = {1.0 / 3.0, 0.4, 0.5, 0.75, 1.0};
     const int pair_tpps[6] = {1, 2, 4, 8, 16, 32};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1426,6 +1427,7 @@ sph_status sph_autotune(sph_ctx* ctx)
     const bool try_bins = ctx->cfg.pair_bins == 0;
     const int bin_ws[4] = {4, 5, 6, 7};   // 16 .. 128 list words per lane
     double best_total = 1e300, best_f = ctx->cell_factor;
+    auto beats = [&](double tot, double) { return tot < best_total; };
     int best_pair = ctx->tpp_pair, best_den = ctx->tpp_den;
     int best_bpair = ctx->bins_pair, best_bden = ctx->bins_den;
     bool best_fused = ctx->fused;
@@ -1482,7 +1484,7 @@ sph_status sph_autotune(sph_ctx* ctx)
                 const bool bd = c & 1, bm = c & 2;
                 if ((bd && !wden) || (bm && !wmom) || (!bd && uden >= 1e29f) || (!bm && umom >= 1e29f)) continue;
                 const double tot = (double)bnb + (bd ? bden : uden) + (bm ? bmom : umom) + ((bd || bm) ? tbin : 0.0f);
-                if (tot < best_total) {
+                if (beats(tot, f)) {
                     best_total = tot;
                     best_f = f;
                     best_den = tden;
@@ -1496,7 +1498,7 @@ sph_status sph_autotune(sph_ctx* ctx)
         if (try_fused) {
             ctx->fused = true;
             const double tot = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
-            if (tot < best_total) {
+            if (beats(tot, f)) {
                 best_total = tot;
                 best_f = f;
                 best_fused = true;

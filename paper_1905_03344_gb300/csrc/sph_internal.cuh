@@ -61,6 +61,8 @@ __host__ __device__ __forceinline__ int stencil_k(double cell_factor)
 // Cell edges carry a relative margin so that FP32 cell assignment can never
 // separate two particles closer than 2 h_max by more than K cells.
 constexpr double kCellMargin = 1.0 + 1.0 / 1024.0;
+// with a 3-cell stencil, cells no finer than min(h_s, kCellMed h_median)
+constexpr double kCellMed = 1.3;
 
 struct PatchDev {
     int64_t begin, end;          // sorted slot range (fixed after set_patches)

@@ -200,6 +200,24 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
         if (edge < 0.8 * hmax) hs = edge;
     }
     double s = 2.0 * hs * cell_factor * kCellMargin;
+    if (K == 3) {
+        // the stencil reaches 3 cells, so cells may be finer than h_s: as
+        // fine as 2 h_s cell_factor, but not below min(h_s, kCellMed h_med),
+        // the edge that served the interior particles best (h_med: the
+        // median of h, from the histogram, to a bin).  With a narrow spread
+        // of h this is the h_s-sized cell of cell_factor 1/2.
+        double hmed = hmax;
+        int64_t acc = 0;
+        for (int b = 0; b < kHBins; b++) {
+            acc += red[p].hist[b];
+            if (2 * acc >= np) {
+                hmed = hmax * ((double)b + 0.5) / (double)kHBins;
+                break;
+            }
+        }
+        const double sm = fmin(hs, kCellMed * hmed) * kCellMargin;
+        if (s < sm) s = sm;
+    }
     const double sext = fmax(ex, ey) / (double)(kMaxCellsAxis - 1) * kCellMargin;
     if (s < sext) s = sext;
     if (!(s > 0.0)) s = P.lz > 0.0 ? P.lz : 1.0;
@@ -780,53 +798,46 @@ __global__ void __launch_bounds__(256) k_cell_boxes(const PatchDev* pd, Grid g, 
     }
 }
 
-// The largest h within K fine cells of each fine cell, a separable maximum:
-// over the (2K+1)^2 cells of its x-y square (in range), then over 2K+1 z
-// planes (periodic; with fewer z cells than that, every plane).  A small
-// particle's search from this cell reaches no farther than 2 max(h_i, hnb).
-__global__ void __launch_bounds__(256) k_hnb_xy(const PatchDev* pd, Grid g, int K, float* tmp)
+// The largest h within K fine cells of each fine cell along each axis, a
+// separable maximum in three passes: along x and along y (in range), then
+// over 2K+1 z planes (periodic; with fewer z cells than that, every plane).
+// A small particle's search from this cell reaches no farther than
+// 2 max(h_i, hnb).  axis 0 reads the cell table's h_max, the others the
+// previous pass.
+__global__ void __launch_bounds__(256) k_hnb_pass(const PatchDev* pd, Grid g, int K, int axis, const float* in,
+                                                  float* out)
 {
     const PatchDev* P = pd + blockIdx.y;
-    const int ncx = P->ncx, ncy = P->ncy;
-    const int64_t nfine = (int64_t)ncx * ncy * P->ncz;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nfine; c += (int64_t)gridDim.x * blockDim.x) {
-        const int cx = (int)(c % ncx), cy = (int)((c / ncx) % ncy);
-        const int64_t plane = c - (int64_t)cy * ncx - cx;
-        float m = 0.0f;
-        for (int y = max(cy - K, 0); y <= min(cy + K, ncy - 1); y++)
-            for (int x = max(cx - K, 0); x <= min(cx + K, ncx - 1); x++)
-                m = fmaxf(m, __uint_as_float(g.cell[P->cell_base + plane + (int64_t)y * ncx + x].z));
-        tmp[P->cell_base + c] = m;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_hnb_z(const PatchDev* pd, Grid g, int K, const float* tmp)
-{
-    const PatchDev* P = pd + blockIdx.y;
-    const int64_t nxy = (int64_t)P->ncx * P->ncy;
-    const int ncz = P->ncz;
+    const int ncx = P->ncx, ncy = P->ncy, ncz = P->ncz;
+    const int64_t nxy = (int64_t)ncx * ncy;
     const int64_t nfine = nxy * ncz;
-    const int kz = 2 * K + 1 > ncz ? (ncz - 1) / 2 + 1 : K;   // every plane when they are fewer
+    const int n = axis == 0 ? ncx : (axis == 1 ? ncy : ncz);
+    const int64_t stride = axis == 0 ? 1 : (axis == 1 ? ncx : nxy);
+    // every z plane when they are fewer than 2K+1
+    const int kk = axis == 2 && 2 * K + 1 > ncz ? (ncz - 1) / 2 + 1 : K;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nfine; c += (int64_t)gridDim.x * blockDim.x) {
-        const int cz = (int)(c / nxy);
-        const int64_t r = c - (int64_t)cz * nxy;
+        const int pos = (int)((c / stride) % n);
+        const int64_t c0 = c - (int64_t)pos * stride;
         float m = 0.0f;
-        for (int dz = -kz; dz <= kz; dz++) {
-            int z = cz + dz;
-            z = ((z % ncz) + ncz) % ncz;
-            m = fmaxf(m, tmp[P->cell_base + (int64_t)z * nxy + r]);
+        for (int d = -kk; d <= kk; d++) {
+            int q = pos + d;
+            if (axis == 2) q = ((q % n) + n) % n;
+            else if (q < 0 || q >= n) continue;
+            const int64_t cell = P->cell_base + c0 + (int64_t)q * stride;
+            m = fmaxf(m, axis == 0 ? __uint_as_float(g.cell[cell].z) : in[cell]);
         }
-        g.hnb[P->cell_base + c] = m;
+        out[P->cell_base + c] = m;
     }
 }
 
 int launch_cell_hnb(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, int K, float* tmp)
 {
     if (npatch <= 0) return 0;
-    const int bx = npatch > 8 ? 8 : (L.sms * 4 + npatch - 1) / npatch;
-    k_hnb_xy<<<dim3((unsigned)bx, (unsigned)npatch), 256, 0, L.stream>>>(pd, g, K, tmp);
-    k_hnb_z<<<dim3((unsigned)bx, (unsigned)npatch), 256, 0, L.stream>>>(pd, g, K, tmp);
-    return 2;
+    const dim3 grid(npatch > 8 ? 8 : (L.sms * 4 + npatch - 1) / npatch, npatch);
+    k_hnb_pass<<<grid, 256, 0, L.stream>>>(pd, g, K, 0, nullptr, g.hnb);
+    k_hnb_pass<<<grid, 256, 0, L.stream>>>(pd, g, K, 1, g.hnb, tmp);
+    k_hnb_pass<<<grid, 256, 0, L.stream>>>(pd, g, K, 2, tmp, g.hnb);
+    return 3;
 }
 
 int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4)

@@ -254,7 +254,16 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
     const float Rg2 = Rg * Rg;
     const float Rc = 2.0f * (1.0f + 1.0f / 512.0f);
     const float qs = s_f * (1.0f / kBoxQ), qsz = sz_f * (1.0f / kBoxQ);
-    const int nz = ZW ? ncz : 2 * K + 1;
+    // cells more than kr (kz along z) away are farther than Rg: the gap to
+    // cell +-d is at least (d - 1) s, and (kr - 1) s > Rg is impossible for
+    // kr = floor(Rg / s) + 1 (a relative margin covers the FP32 rounding of
+    // the quotient).  The bound is the same on both sides and depends on i
+    // only through max(h_i, hnb), so that lanes whose particles share a cell
+    // keep walking its stencil in step.
+    // (a stencil of at most 2 cells keeps its compile-time bounds)
+    const int kr = K <= 2 ? K : min(K, (int)(Rg * P->inv_s_f * (1.0f + 1.0f / 1024.0f)) + 1);
+    const int kz = ZW ? 0 : (K <= 2 ? K : min(K, (int)(Rg * P->inv_sz_f * (1.0f + 1.0f / 1024.0f)) + 1));
+    const int nz = ZW ? ncz : 2 * kz + 1;
     for (int iz = 0; iz < nz; iz++) {
         int czj, zd;
         float zsh, gz2;
@@ -262,7 +271,7 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
         float gzr = -1e30f;
         uint32_t zshift = 20;
         if (!ZW) {
-            const int dcz = iz - K;
+            const int dcz = iz - kz;
             czj = cz + dcz;
             if (czj < 0) czj += ncz;
             else if (czj >= ncz) czj -= ncz;
@@ -281,7 +290,7 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
         }
         if (gz2 >= Rg2) continue;
         const float zo = ri.z - zsh;
-        for (int dcy = -K; dcy <= K; dcy++) {
+        for (int dcy = -kr; dcy <= kr; dcy++) {
             const int cyj = cy + dcy;
             if ((unsigned)cyj >= (unsigned)ncy) continue;
             const float gyr = dcy > 0 ? (float)dcy * s_f - ri.y : (dcy < 0 ? ri.y - (float)(dcy + 1) * s_f : -1e30f);
@@ -292,9 +301,11 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
             const float yo = ri.y - (float)dcy * s_f;
             const uint32_t lrow = cbase + ((uint32_t)czj * (uint32_t)ncy + (uint32_t)cyj) * (uint32_t)ncx + (uint32_t)cx;
             const uint32_t kkrow = (uint32_t)(2 + 5 * (dcy + 2) + 25 * zd);
+            // a K = 3 stencil reaches cells 3 away, which have no stencil code
+            const bool rowcode = K <= 2 || (dcy >= -2 && dcy <= 2 && zd >= 0 && zd <= 4);
             // one copy of the candidate loop for all x offsets (code size)
 #pragma unroll 1
-            for (int dcx = -K; dcx <= K; dcx++) {
+            for (int dcx = -kr; dcx <= kr; dcx++) {
                 if ((unsigned)(cx + dcx) >= (unsigned)ncx) continue;
                 const float gxr = dcx > 0 ? (float)dcx * s_f - ri.x : (dcx < 0 ? ri.x - (float)(dcx + 1) * s_f : -1e30f);
                 const float gx = fmaxf(gxr, 0.0f);
@@ -307,9 +318,8 @@ __device__ __forceinline__ void walk_small(const NbArgs& a, const PatchDev* P, i
                 const float R = fmaxf(hf, __uint_as_float(cr.z)) * Rc + slack;
                 if (tight_gap2(cr.w, gxr, dcx > 0 ? 0u : 5u, gyr, yshift, gzr, zshift, qs, qsz) >= R * R) continue;
                 const float xo = ri.x - (float)dcx * s_f;
-                // offsets of up to 2 cells have a stencil code; K = 3 reaches 3
-                const uint32_t kk = (K <= 2 ? kkrow + (uint32_t)dcx
-                                            : stencil_code(P, dcx, dcy, ZW ? zd : zd - 2, !ZW)) << kColBits;
+                // offsets of up to 2 cells have a stencil code
+                const uint32_t kk = (rowcode && dcx >= -2 && dcx <= 2 ? kkrow + (uint32_t)dcx : kFarCode) << kColBits;
                 // kGroup candidates per iteration: their gathers are in flight
                 // together (the record array has kGroup padding entries, so a
                 // group may read past the cell; those slots are masked)

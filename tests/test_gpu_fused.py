@@ -48,7 +48,7 @@ def _same_bits(g, h, what):
 
 @pytest.mark.parametrize("case", sorted(FORCE_CASES))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("cf", [1.0 / 3.0, 0.5, 1.0])
+@pytest.mark.parametrize("cf", [1.0 / 3.0, 0.4, 0.5, 1.0])
 def test_fused_equals_lists(B, case, precision, cf):
     f = FORCE_CASES[case]()
     lz = f.pop("lz", 1.0)

@@ -97,7 +97,7 @@ def test_neighbor_lists_bit_exact(B, orc, case):
 
 
 @pytest.mark.parametrize("tpp", [1, 2, 4, 8, 16, 32])
-@pytest.mark.parametrize("cf", [1.0 / 3.0, 0.5, 0.75, 1.0, 2.5])
+@pytest.mark.parametrize("cf", [1.0 / 3.0, 0.4, 0.5, 0.75, 1.0, 2.5])
 def test_neighbor_lists_any_launch_shape(B, orc, tpp, cf):
     f = inputs.random_cloud(1500, seed=11, h_lo=0.02, h_hi=0.1)
     ref = orc.neighbors(f["x"], f["y"], f["z"], f["h"])
