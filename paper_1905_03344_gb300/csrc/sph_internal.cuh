@@ -7,7 +7,8 @@
 // patch is big).  A uniform grid of cells with edge s >= 2 h_s cell_factor
 // covers the bounding box in x, y and the period lz in z; a small particle
 // searches the (2K+1)^3 cells around its own (K = 1 for cell_factor >= 1,
-// K = 2 below) for small neighbours, pruned by each cell's largest h.  Big
+// 2 for >= 1/2, 3 below) for small neighbours, pruned by the largest h
+// around its cell and by each cell's own largest h.  Big
 // particles are indexed separately by coarse cells (aligned blocks of 2^kc
 // fine cells with edge >= 2 h_max), which every particle searches for big
 // neighbours; a big particle searches the fine grid as far as its own 2 h.
@@ -235,7 +236,7 @@ struct NbArgs {
     int64_t pool_cap;                    // entries the pool holds (max_pairs + slack)
     int* status;
 };
-// K: stencil half-extent of every patch (1 for cell_factor >= 1, else 2)
+// K: stencil half-extent of every patch (1 for cell_factor >= 1, 2 for >= 1/2, else 3)
 // exact = 1: the neighbour lists and n_i; exact = 0: the candidate superset
 // of reused lists (every candidate within the grid's scaled search radius)
 int launch_nb_lists(const Launch& L, const NbArgs& a, int K, int exact);

@@ -154,7 +154,8 @@ int launch_reset_red(const Launch& L, int npatch, PatchRed* red)
 // lowest histogram bin above which at most 1/kBigShare of the patch lies (h_s
 // = h_max, no big particles, when that edge is above 0.8 h_max).  Fine cell
 // edge s = 2 h_s cell_factor (with margin), stencil half-extent K = 1 for
-// cell_factor >= 1, 2 for >= 1/2, else 3, so K s >= 2 h_s.  Coarse cells are aligned blocks
+// cell_factor >= 1, 2 for >= 1/2, else 3, so K s >= 2 h_s; with K = 3 the
+// edge is also at least min(h_s, kCellMed h_median).  Coarse cells are aligned blocks
 // of 2^kc fine cells with 2^kc s >= 2 h_max, so the 3 x 3 x 3 coarse block
 // around a particle holds every big particle that can reach it.  At most 128
 // cells per axis and cell_cap fine + coarse cells per patch (s grows if not).

@@ -7,7 +7,8 @@
 // one patch.  The search has up to three parts, each visiting every
 // candidate of its kind once:
 //   small i, small j: the (2K+1)^3 fine cells around i's cell (template K),
-//     pruned by distance against 2 max(h_i, h_max(cell));
+//     pruned by distance against 2 max(h_i, hnb) (hnb: the largest h around
+//     i's cell) and then against 2 max(h_i, h_max(cell));
 //   big i, small j:   the fine cells within 2 h_i of i (runtime extent);
 //   any i, big j:     the 3 x 3 x 3 coarse cells around i's coarse cell
 //     (only when the patch has big particles).
