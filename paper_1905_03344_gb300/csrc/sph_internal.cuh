@@ -32,7 +32,6 @@ constexpr uint32_t kColMask = (1u << kColBits) - 1u;
 constexpr int64_t kMaxParticles = int64_t(1) << kColBits;
 constexpr int kMaxPatches = 256;
 constexpr int kItemChunk = 4096;               // particles per work item
-constexpr int kStencilCells = 125;             // (2K+1)^3 for K <= 2
 constexpr uint32_t kFarCode = 127;             // column stencil code: offset from the cell coordinates
 #ifndef SPH_BIG_SHARE
 #define SPH_BIG_SHARE 64

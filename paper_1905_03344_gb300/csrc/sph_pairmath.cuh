@@ -417,7 +417,7 @@ struct PairTerms2 {
 // operations, in the halves of packed FP32x2 values (mj = 0 in a half makes
 // its terms 0)
 __device__ __forceinline__ PairTerms2 momentum_pair2(float2 dx, float2 dy, float2 dz, const float4& vi,
-                                                     const float4& ti, float wi5, const float4& va,
+                                                     const float4& ti, const float4& va,
                                                      const float4& vb, const float4& ta, const float4& tb,
                                                      float2 mj, const MomConst& K)
 {
@@ -603,7 +603,7 @@ __device__ __forceinline__ void momentum_chunk(const PairSrc& src, const PairSid
                 col_dx<ZW>(src, I, cwb, qb, dxb, dyb, dzb);
             }
             const PairTerms2 t = momentum_pair2(make_float2(dxa, dxb), make_float2(dya, dyb), make_float2(dza, dzb),
-                                                vi, ti, wi5, va, vb, ta, tb, make_float2(qa.w, hb ? qb.w : 0.0f), K);
+                                                vi, ti, va, vb, ta, tb, make_float2(qa.w, hb ? qb.w : 0.0f), K);
             px = add2(px, t.ax);
             py = add2(py, t.ay);
             pz = add2(pz, t.az);
