@@ -370,6 +370,7 @@ def main():
     rebuilds = sim.list_rebuilds() - rb0
     pairs = sim.pair_count(reset=True)
     prof = sim.profile()
+    cf_end = binding.sph_get_tuning(sim.ctx)[1]
     sim.profile(False)
 
     # the same stretch of steps replayed from captured CUDA graphs: back to
@@ -467,7 +468,7 @@ def main():
                    "threads_per_particle": tpp, "threads_per_particle_density": tpp_den,
                    "row_length_bins": {"density_words_per_lane": bins_den, "momentum_words_per_lane": bins_mom,
                                        "note": "0: uniform lanes per particle"},
-                   "cell_factor": cf, "pair_mode": mode,
+                   "cell_factor": cf, "cell_factor_end": cf_end, "pair_mode": mode,
                    "list_skin": args.skin, "searches_in_timed_steps": rebuilds if args.skin > 0 else args.steps,
                    "timed": "K steps with CUDA events between phases (no graph)"},
         "steps_per_s": steps_per_s, "pairs_per_step": pairs_per_step,

@@ -113,7 +113,9 @@ typedef struct {
                                (h_s: the patch's class threshold of h);
                                below 1/2 the stencil reaches 3 cells and the
                                edge is at least min(h_s, 1.3 h_median).
-                               0 (default): 1/2 */
+                               0 (default): 1/2, switched by sph_step between
+                               1/2 and 0.4 as the state's spread of h asks;
+                               any other value stays fixed */
     double list_skin;       /* 0 (default): every step sorts and searches.
                                skin > 0 (at most 1; list mode only): the search
                                lists the candidate superset r < 2 (1 + skin)
@@ -247,7 +249,11 @@ sph_status sph_momentum_energy(sph_ctx* ctx);
  * Courant dt_n = min(C min h/c, dt_growth dt_{n-1}) per patch, kick
  * v_{n+1/2} = v_{n-1/2} + a_n (dt_n + dt_{n-1})/2, drift x += v_{n+1/2} dt_n
  * (z wrapped), Adams-Bashforth energy, h adaptation, conserved sums.
- * dt_last (nullable, host) receives patch 0's last dt.
+ * dt_last (nullable, host) receives patch 0's last dt.  With a cell factor
+ * of 1/2 or 0.4 that came from the default or from sph_autotune, the call
+ * ends by taking the cell grid's vote of its last sort for the next call:
+ * 0.4 once the spread of h is wide but smooth in space, 1/2 again when it is
+ * not (see cell_factor); the choice depends on the state alone.
  * Errors: SPH_EOVERFLOW, SPH_ENONFINITE, SPH_ETIMEOUT, SPH_ESTATE. */
 sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last);
 

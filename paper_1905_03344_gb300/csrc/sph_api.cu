@@ -99,6 +99,12 @@ struct sph_ctx {
     uint32_t* bin_bounds = nullptr; // [kPairOctaves + 1] octave starts in bin_order
     bool bins_valid = false;       // bin_order belongs to the current lists
     double cell_factor = 0.5;
+    // the cell factor came from the default or the autotuner: between 1/2 and
+    // 0.4 it follows the cell grid's vote (cf_vote, taken at every sort)
+    bool cf_auto = true;
+    unsigned long long* cf_vote = nullptr;
+    unsigned long long* h_cf_vote = nullptr;   // pinned
+    int64_t cf_switches = 0;
     int mixed = 1;
     bool fused = false;            // pair sums without lists (SPH_PAIRS_FUSED in effect)
     // reused candidate supersets (list_skin > 0, list mode)
@@ -417,6 +423,7 @@ void enqueue_sort(sph_ctx* ctx, bool superset = false)
                                        superset ? ctx->hsearch_pre : nullptr, superset ? ctx->skinref.h0 : nullptr);
         ctx->launches += launch_cell_boxes(L, ctx->npatch, ctx->pd, ctx->grid, ctx->rec.r4);
         ctx->launches += launch_cell_hnb(L, ctx->npatch, ctx->pd, ctx->grid, stencil_k(ctx->cell_factor), ctx->hnb_tmp);
+        ctx->launches += launch_cell_vote(L, ctx->npatch, ctx->pd, ctx->grid, ctx->cf_vote);
         ctx->cur = nxt;
     }
     ctx->fresh = false;
@@ -769,6 +776,7 @@ void sph_destroy(sph_ctx* ctx)
         if (p) cudaFree(p);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_skin_flag) cudaFreeHost(ctx->h_skin_flag);
+    if (ctx->h_cf_vote) cudaFreeHost(ctx->h_cf_vote);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -795,6 +803,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         return fail(nullptr, SPH_EINVAL, "max_particles must be in [1, 2^25]");
     if (cfg.max_patches < 1 || cfg.max_patches > kMaxPatches)
         return fail(nullptr, SPH_EINVAL, "max_patches must be in [1, 256]");
+    const bool cf_default = cfg.cell_factor == 0.0;
     if (cfg.cell_factor == 0.0) cfg.cell_factor = 0.5;
     if (!(cfg.cell_factor >= 1.0 / 3.0 && cfg.cell_factor <= 4.0))
         return fail(nullptr, SPH_EINVAL, "cell_factor must be in [1/3, 4]");
@@ -834,6 +843,7 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
     ctx->mixed = cfg.precision == SPH_MIXED;
     ctx->kernel_b = kernel_norm(cfg.kernel, cfg.kernel_n);
     ctx->cell_factor = cfg.cell_factor;
+    ctx->cf_auto = cf_default;
     if (t) ctx->tpp_pair = ctx->tpp_den = t;
     if (pb > 0) {
         int w = 0;
@@ -912,6 +922,8 @@ sph_status sph_create(const sph_config* cfg_in, sph_ctx** out)
         if (ok && cudaMallocHost(&ctx->h_skin_flag, sizeof(int)) != cudaSuccess) ok = false;
     }
     ctx->grid.patch_of = ctx->patch_of;
+    ok = ok && dalloc(ctx, ctx->cf_vote, 2);
+    if (ok && cudaMallocHost(&ctx->h_cf_vote, 2 * sizeof(unsigned long long)) != cudaSuccess) ok = false;
     if (ok && cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
         sph_destroy(ctx);
@@ -1183,6 +1195,24 @@ sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double* dt_last)
     if (st != SPH_OK) return st;
     if (dt_last) {
         CK(cudaMemcpy(dt_last, &ctx->pd[0].dt, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    // an automatic cell factor of 1/2 or 0.4 follows the vote of the last
+    // sort: the 3-cell stencil over median-sized cells (0.4) once most
+    // non-empty cells of patches with a wide spread of h see no h above
+    // 0.8 h_s around them, cells of edge h_s (1/2) again when few do.  The
+    // vote depends on the state alone, so a run is reproducible for a given
+    // sequence of calls; the new grid takes effect at the next call.
+    if (ctx->cf_auto && (ctx->cell_factor == 0.4 || ctx->cell_factor == 0.5)) {
+        CK(cudaMemcpy(ctx->h_cf_vote, ctx->cf_vote, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        const unsigned long long ne = ctx->h_cf_vote[0], nn = ctx->h_cf_vote[1];
+        double want = ctx->cell_factor;
+        if (ctx->cell_factor == 0.5 && nn * 20 > ne * 11) want = 0.4;        // above 55 %
+        else if (ctx->cell_factor == 0.4 && nn * 10 < ne * 3) want = 0.5;    // below 30 %
+        if (want != ctx->cell_factor) {
+            ctx->cell_factor = want;
+            ctx->cf_switches++;
+            destroy_graphs(ctx);
+        }
     }
     return SPH_OK;
 }
@@ -1508,6 +1538,7 @@ sph_status sph_autotune(sph_ctx* ctx)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->cell_factor = best_f;
+    ctx->cf_auto = true;
     ctx->tpp_pair = best_pair;
     ctx->tpp_den = best_den;
     ctx->bins_pair = best_bpair;

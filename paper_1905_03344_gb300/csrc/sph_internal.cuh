@@ -75,6 +75,7 @@ struct PatchDev {
     int32_t nbig;                // big particles (h > hs), counted by the key kernel
     double hs;                   // class threshold: small iff h <= hs
     float hs_f;
+    double hmed;                 // median of h (histogram bin centre)
     int32_t kc;                  // coarse cell = 2^kc fine cells per axis
     int32_t ncxc, ncyc, nczc;    // coarse grid
     int32_t zmode_c;             // 0: 3 distinct coarse z cells; 1: all of them
@@ -214,6 +215,10 @@ int launch_refresh_records(const Launch& L, int64_t n, const State& s, const uin
 int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4);
 // g.hnb for stencil half-extent K (tmp: one float per cell)
 int launch_cell_hnb(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, int K, float* tmp);
+// the state's vote for the grid of the next sort (vote[0]: non-empty fine
+// cells, vote[1]: those whose hnb is below 0.8 h_s in a patch with h_s above
+// 1.4 h_median); vote is cleared here
+int launch_cell_vote(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, unsigned long long* vote);
 // temporary words of the device-wide exclusive scan over n values
 int64_t scan_tmp_words(int64_t n);
 

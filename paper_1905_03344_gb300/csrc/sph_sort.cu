@@ -201,13 +201,9 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
         if (edge < 0.8 * hmax) hs = edge;
     }
     double s = 2.0 * hs * cell_factor * kCellMargin;
-    if (K == 3) {
-        // the stencil reaches 3 cells, so cells may be finer than h_s: as
-        // fine as 2 h_s cell_factor, but not below min(h_s, kCellMed h_med),
-        // the edge that served the interior particles best (h_med: the
-        // median of h, from the histogram, to a bin).  With a narrow spread
-        // of h this is the h_s-sized cell of cell_factor 1/2.
-        double hmed = hmax;
+    // the median of h, from the histogram, to a bin
+    double hmed = hmax;
+    {
         int64_t acc = 0;
         for (int b = 0; b < kHBins; b++) {
             acc += red[p].hist[b];
@@ -216,6 +212,12 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
                 break;
             }
         }
+    }
+    if (K == 3) {
+        // the stencil reaches 3 cells, so cells may be finer than h_s: as
+        // fine as 2 h_s cell_factor, but not below min(h_s, kCellMed h_med),
+        // the edge that served the interior particles best.  With a narrow
+        // spread of h this is the h_s-sized cell of cell_factor 1/2.
         const double sm = fmin(hs, kCellMed * hmed) * kCellMargin;
         if (s < sm) s = sm;
     }
@@ -269,6 +271,7 @@ __global__ void k_grid_params(int npatch, const PatchRed* red, PatchDev* pd, dou
     P.hmax_f = (float)hmax;
     P.hs = hs;
     P.hs_f = (float)hs;
+    P.hmed = hmed;
     P.nbig = 0;
     P.kc = kc;
     P.ncxc = (int)ncxc;
@@ -839,6 +842,44 @@ int launch_cell_hnb(const Launch& L, int npatch, const PatchDev* pd, const Grid&
     k_hnb_pass<<<grid, 256, 0, L.stream>>>(pd, g, K, 1, g.hnb, tmp);
     k_hnb_pass<<<grid, 256, 0, L.stream>>>(pd, g, K, 2, tmp, g.hnb);
     return 3;
+}
+
+// The vote of the cell grid for the next sort: the fine cells that hold
+// particles, and among them, in a patch whose spread of h is wide (h_s >
+// 1.4 h_median), those whose particles' neighbourhoods have no h above 0.8
+// h_s.  Many such cells (h wide but smooth in space, as behind the free
+// surface of a patch) favour a 3-cell stencil over median-sized cells; few
+// (h varying from particle to particle) favour cells of edge h_s.
+__global__ void __launch_bounds__(256) k_cell_vote(const PatchDev* pd, Grid g, unsigned long long* vote)
+{
+    const PatchDev* P = pd + blockIdx.y;
+    const int64_t nfine = (int64_t)P->ncx * P->ncy * P->ncz;
+    const bool wide = P->hs > 1.4 * P->hmed;
+    const float lim = 0.8f * P->hs_f;
+    uint32_t ne = 0, nn = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nfine; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 cr = g.cell[P->cell_base + c];
+        if (cr.x >= cr.y) continue;
+        ne++;
+        nn += (uint32_t)(wide && g.hnb[P->cell_base + c] < lim);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ne += __shfl_xor_sync(0xffffffffu, ne, o);
+        nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    }
+    if ((threadIdx.x & 31) == 0 && ne) {
+        atomicAdd(&vote[0], (unsigned long long)ne);
+        atomicAdd(&vote[1], (unsigned long long)nn);
+    }
+}
+
+int launch_cell_vote(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, unsigned long long* vote)
+{
+    cudaMemsetAsync(vote, 0, 2 * sizeof(unsigned long long), L.stream);
+    if (npatch <= 0) return 0;
+    const dim3 grid(npatch > 8 ? 8 : (L.sms * 4 + npatch - 1) / npatch, npatch);
+    k_cell_vote<<<grid, 256, 0, L.stream>>>(pd, g, vote);
+    return 1;
 }
 
 int launch_cell_boxes(const Launch& L, int npatch, const PatchDev* pd, const Grid& g, const float4* r4)
