@@ -61,7 +61,8 @@ NB_BYTES_PER_PARTICLE = 48
 # dram__bytes_write.sum divided by the launch's 8.54e8 list entries; see
 # profiles/launches_square_patch_200cubed.md), scaled to the benchmark's
 # launch by its entries.  None once the kernel has changed since; the
-# momentum figure is that of its 2-lanes-per-particle instantiation.
+# momentum figure is that of its 2-lanes-per-particle instantiation, the
+# search's that of both its 2- and 3-cell stencils (5.70 B each).
 NB_DRAM_BYTES_PER_ENTRY = 5.70
 MOMENTUM_DRAM_BYTES_PER_ENTRY = 7.88
 MOMENTUM_DRAM_TPP = 2
