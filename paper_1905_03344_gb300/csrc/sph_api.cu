@@ -731,7 +731,7 @@ void sph_config_default(sph_config* c)
     c->dt_fixed = 0.0;
     c->adapt_h = 1;
     c->threads_per_particle = 0;
-    c->cell_factor = 0.5;
+    c->cell_factor = 0.0;       // automatic: 1/2, then as the cell grid votes
     c->max_particles = 1 << 20;
     c->max_pairs = 0;
     c->max_patches = 1;

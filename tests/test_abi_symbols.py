@@ -46,7 +46,7 @@ def test_config_struct_matches_header_defaults(lib):
     assert c.gamma == pytest.approx(5.0 / 3.0)
     assert c.courant == 0.2 and c.dt_growth == 1.1 and c.n_target == 100.0
     assert c.av_alpha == 1.0 and c.av_beta == 2.0 and c.av_eps == 0.01
-    assert c.lz == 1.0 and c.adapt_h == 1 and c.cell_factor == 0.5
+    assert c.lz == 1.0 and c.adapt_h == 1 and c.cell_factor == 0.0
 
 
 def test_status_strings(lib):
