@@ -1457,7 +1457,6 @@ sph_status sph_autotune(sph_ctx* ctx)
     const bool try_bins = ctx->cfg.pair_bins == 0;
     const int bin_ws[4] = {4, 5, 6, 7};   // 16 .. 128 list words per lane
     double best_total = 1e300, best_f = ctx->cell_factor;
-    auto beats = [&](double tot, double) { return tot < best_total; };
     int best_pair = ctx->tpp_pair, best_den = ctx->tpp_den;
     int best_bpair = ctx->bins_pair, best_bden = ctx->bins_den;
     bool best_fused = ctx->fused;
@@ -1514,7 +1513,7 @@ sph_status sph_autotune(sph_ctx* ctx)
                 const bool bd = c & 1, bm = c & 2;
                 if ((bd && !wden) || (bm && !wmom) || (!bd && uden >= 1e29f) || (!bm && umom >= 1e29f)) continue;
                 const double tot = (double)bnb + (bd ? bden : uden) + (bm ? bmom : umom) + ((bd || bm) ? tbin : 0.0f);
-                if (beats(tot, f)) {
+                if (tot < best_total) {
                     best_total = tot;
                     best_f = f;
                     best_den = tden;
@@ -1528,7 +1527,7 @@ sph_status sph_autotune(sph_ctx* ctx)
         if (try_fused) {
             ctx->fused = true;
             const double tot = timeit([&] { enqueue_density(ctx); enqueue_momentum(ctx); });
-            if (beats(tot, f)) {
+            if (tot < best_total) {
                 best_total = tot;
                 best_f = f;
                 best_fused = true;
